@@ -1,0 +1,346 @@
+"""Pins of the oracle's polar quadtree (Sec. 4.1) and Barnes-Hut walk (Sec. 4.2).
+
+Independent references:
+  * hand-built keys for points whose normalised coordinates are exact dyadics;
+  * tree invariants (every point in one leaf, counts add up, points inside
+    their cell bounds, r_cell >= the largest distance between the cell's points);
+  * a second construction (key-sorted) that must reproduce the literally
+    inserted tree exactly;
+  * a pure-Python implementation of the literal algorithm for tiny n
+    (insertion with leaf capacity one, depth-first walk with the criterion
+    r_cell / d < theta evaluated with math.acosh);
+  * theta = 0 (no approximation) equals the exact gradient, the error falls
+    as theta -> 0, and at theta = 0.5 it lies in the decade the paper reports
+    (Table GradientAndCostFunctionErrors).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_13708_gb300 import inputs
+
+L = oracle.LEVELS
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def interleave_py(qa, qb, levels=L):
+    k = 0
+    for b in range(levels):
+        k |= ((qa >> b) & 1) << (2 * b + 1)
+        k |= ((qb >> b) & 1) << (2 * b)
+    return k
+
+
+def test_keys_hand_built():
+    # radii 0.125 .. 0.625 make the normalised radius an exact dyadic;
+    # angles 0, pi/4, pi/2, pi give phi^ = 0, 1/8, 1/4, 1/2.
+    a = 0.375 / math.sqrt(2)
+    y = np.array([[0.125, 0.0], [0.0, 0.625], [-0.375, 0.0], [a, a]])
+    k, b = oracle.keys(y)
+    assert b[0] == 0.125 and b[1] == 0.625
+    top = (1 << L) - 1
+    r_hat = [0.0, 1.0, 0.5, (math.hypot(a, a) - 0.125) / 0.5]
+    phi_hat = [0.0, 0.25, 0.5, 0.125]
+    for j in range(4):
+        qa = min(int(math.floor(r_hat[j] * (1 << L))), top)
+        qb = min(int(math.floor(phi_hat[j] * (1 << L))), top)
+        assert int(k[j]) == interleave_py(qa, qb)
+    assert int(k[0]) == 0
+    assert int(k[1]) == interleave_py(top, 1 << (L - 2))
+    assert int(k[2]) == interleave_py(1 << (L - 1), 1 << (L - 1))
+    # digit 1 (the root split) is 2 * radial bit + angular bit
+    assert [int(x) >> (2 * L - 2) for x in k] == [0, 2, 3, 2 * (r_hat[3] >= 0.5) + 0]
+
+
+def embeddings():
+    rng = np.random.default_rng(11)
+    out = {"gauss": rng.normal(0, 0.2, (400, 2))}
+    x, lab = inputs.gaussian_mixture(600, 10, 6, 1)
+    out["spread"] = inputs.spread_embedding(lab, 3)
+    d = rng.normal(0, 0.25, (100, 2))
+    d *= np.minimum(1.0, 0.99 / np.linalg.norm(d, axis=1))[:, None]
+    out["dups"] = np.concatenate([d, d[:20], d[:5]])
+    out["tiny"] = rng.normal(0, 1e-3, (50, 2))
+    return out
+
+
+@pytest.mark.parametrize("name", ["gauss", "spread", "dups", "tiny"])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_key_tree_reproduces_inserted_tree(name, rule):
+    y = embeddings()[name]
+    t0 = oracle.tree_export(y, rule, which=0)
+    t1 = oracle.tree_export(y, rule, which=1)
+    for k in ("depth", "prefix", "count", "first"):
+        assert np.array_equal(t0[k], t1[k]), k
+    assert np.array_equal(t0["ycell"], t1["ycell"])
+    fin = np.isfinite(t0["rcell"])
+    assert np.array_equal(fin, np.isfinite(t1["rcell"]))
+    assert np.array_equal(t0["rcell"][fin], t1["rcell"][fin])
+
+
+def parents_of(t):
+    """Parent index of each exported node (pre-order, depth/prefix)."""
+    par = -np.ones(len(t["depth"]), dtype=np.int64)
+    stack = []
+    for k in range(len(t["depth"])):
+        dk, pk = int(t["depth"][k]), int(t["prefix"][k])
+        while stack:
+            j = stack[-1]
+            dj, pj = int(t["depth"][j]), int(t["prefix"][j])
+            if dj < dk and (pk >> (2 * (dk - dj))) == pj:
+                break
+            stack.pop()
+        par[k] = stack[-1] if stack else -1
+        stack.append(k)
+    return par
+
+
+@pytest.mark.parametrize("name", ["gauss", "spread", "dups"])
+def test_tree_invariants(name):
+    y = embeddings()[name]
+    n = y.shape[0]
+    t = oracle.tree_export(y, 0, 0)
+    keys, b = oracle.keys(y)
+    par = parents_of(t)
+    assert par[0] == -1 and np.all(par[1:] >= 0)
+    # counts add up; the root holds every point
+    assert t["count"][0] == n
+    sums = np.zeros_like(t["count"])
+    np.add.at(sums, par[1:], t["count"][1:])
+    internal = t["first"] < 0
+    assert np.array_equal(sums[internal], t["count"][internal])
+    # leaves: single points cover every non-bucket point exactly once
+    leaves = (t["first"] >= 0) & (t["count"] == 1)
+    buckets = (t["first"] >= 0) & (t["count"] > 1)
+    assert t["count"][leaves].sum() + t["count"][buckets].sum() == n
+    assert np.all(t["depth"][buckets] == L)
+    assert len(set(t["first"][leaves].tolist())) == int(leaves.sum())
+    # every ancestor's prefix is a prefix of the point's key
+    for k in np.nonzero(leaves)[0]:
+        j = int(t["first"][k])
+        a = int(par[k])
+        while a >= 0:
+            da = int(t["depth"][a])
+            assert (int(keys[j]) >> (2 * (L - da))) == int(t["prefix"][a])
+            a = int(par[a])
+    # points lie in their cell's raw bounds, r_cell bounds the distances
+    rlo, rhi = b
+    for k in np.nonzero(internal)[0][:60]:
+        dk = int(t["depth"][k])
+        if dk == 0:
+            continue
+        pk = int(t["prefix"][k])
+        ia = sum(((pk >> (2 * q + 1)) & 1) << q for q in range(dk))
+        ib = sum(((pk >> (2 * q)) & 1) << q for q in range(dk))
+        r0 = rlo + (rhi - rlo) * ia / 2 ** dk
+        r1 = rlo + (rhi - rlo) * (ia + 1) / 2 ** dk
+        members = [j for j in range(n) if (int(keys[j]) >> (2 * (L - dk))) == pk]
+        assert len(members) == t["count"][k]
+        r = np.hypot(y[members, 0], y[members, 1])
+        phi = np.mod(np.arctan2(y[members, 1], y[members, 0]), 2 * np.pi)
+        assert np.all(r >= r0 - 1e-12) and np.all(r <= r1 + 1e-12)
+        assert np.all(phi >= 2 * np.pi * ib / 2 ** dk - 1e-12)
+        assert np.all(phi <= 2 * np.pi * (ib + 1) / 2 ** dk + 1e-12)
+        ym = y[members][:40]
+        dmax = max(oracle.dist(p, q) for p in ym for q in ym)
+        assert t["rcell"][k] >= dmax - 1e-9
+
+
+def test_normalised_decisions_match_raw_midpoints():
+    # Reading R5: cell membership decided on the normalised coordinates must
+    # agree with the paper's (min+max)/2 splits of (r, phi) except for points
+    # within a few ulp of a split line (none at this seed).
+    y = embeddings()["spread"]
+    keys, (rlo, rhi) = oracle.keys(y)
+    r = np.hypot(y[:, 0], y[:, 1])
+    phi = np.mod(np.arctan2(y[:, 1], y[:, 0]), 2 * np.pi)
+    for j in range(y.shape[0]):
+        lo_r, hi_r, lo_p, hi_p = rlo, rhi, 0.0, 2 * np.pi
+        for lev in range(1, 16):
+            mid_r, mid_p = (lo_r + hi_r) / 2, (lo_p + hi_p) / 2
+            up_r, up_p = r[j] >= mid_r, phi[j] >= mid_p
+            digit = (int(keys[j]) >> (2 * (L - lev))) & 3
+            assert digit == 2 * up_r + up_p
+            lo_r, hi_r = (mid_r, hi_r) if up_r else (lo_r, mid_r)
+            lo_p, hi_p = (mid_p, hi_p) if up_p else (lo_p, mid_p)
+
+
+# ---------------------------------------------------------------------------
+# Pure-Python literal Barnes-Hut (tiny n only)
+# ---------------------------------------------------------------------------
+
+def py_dist(a, b):
+    s = (a[0] - b[0]) ** 2 + (a[1] - b[1]) ** 2
+    return math.acosh(1 + 2 * s / ((1 - a[0] ** 2 - a[1] ** 2) * (1 - b[0] ** 2 - b[1] ** 2)))
+
+
+def py_bh(y, theta):
+    n = len(y)
+    r = [math.hypot(*p) for p in y]
+    phi = [math.atan2(p[1], p[0]) % (2 * math.pi) for p in y]
+    rlo, rhi = min(r), max(r)
+    u = [(x - rlo) / (rhi - rlo) for x in r]
+    v = [p / (2 * math.pi) for p in phi]
+
+    class Node:
+        def __init__(s, depth, a, b):
+            s.depth, s.a, s.b, s.kids, s.pts = depth, a, b, {}, []
+
+    root = Node(0, 0, 0)
+    for j in range(n):
+        node = root
+        node.pts.append(j)
+        while True:
+            if len(node.pts) == 1 and not node.kids:
+                break
+            if node.depth == L:
+                break
+            if not node.kids:  # push the resident point down
+                old = node.pts[0]
+                c = node.child_of(old) if hasattr(node, "child_of") else None
+            sc = 2.0 ** -node.depth
+            cr = int(u[j] >= (node.a * sc + (node.a + 1) * sc) / 2)
+            ca = int(v[j] >= (node.b * sc + (node.b + 1) * sc) / 2)
+            if not node.kids and len(node.pts) == 2:
+                old = node.pts[0]
+                orr = int(u[old] >= (node.a * sc + (node.a + 1) * sc) / 2)
+                oa = int(v[old] >= (node.b * sc + (node.b + 1) * sc) / 2)
+                ch = Node(node.depth + 1, 2 * node.a + orr, 2 * node.b + oa)
+                ch.pts.append(old)
+                node.kids[(orr, oa)] = ch
+            key = (cr, ca)
+            if key not in node.kids:
+                ch = Node(node.depth + 1, 2 * node.a + cr, 2 * node.b + ca)
+                ch.pts.append(j)
+                node.kids[key] = ch
+                break
+            node = node.kids[key]
+            node.pts.append(j)
+
+    def midpoint(pts):
+        sg = sx = sy = 0.0
+        for j in pts:
+            n2 = y[j][0] ** 2 + y[j][1] ** 2
+            g = (1 + n2) / (1 - n2)
+            vx, vy = 2 * y[j][0] / (1 + n2), 2 * y[j][1] / (1 + n2)
+            sg += g
+            sx += g * vx
+            sy += g * vy
+        mx, my = sx / sg, sy / sg
+        s = math.sqrt(1 - mx * mx - my * my)
+        return (mx / (1 + s), my / (1 + s))
+
+    def quad_diam(node):
+        sc = 2.0 ** -node.depth
+        r0 = rlo + (rhi - rlo) * node.a * sc
+        r1 = rlo + (rhi - rlo) * (node.a + 1) * sc
+        dp = 2 * math.pi * sc
+        c = [(r0, 0.0), (r1 * math.cos(dp), r1 * math.sin(dp)), (r1, 0.0)]
+        return max(py_dist(c[0], c[1]), py_dist(c[0], c[2]), py_dist(c[2], c[1]))
+
+    def term(yi, yc):
+        # w^2 d dd/dy_i, written from Eq. PoincareDistanceDerivative
+        a = 1 - yi[0] ** 2 - yi[1] ** 2
+        b = 1 - yc[0] ** 2 - yc[1] ** 2
+        s = (yi[0] - yc[0]) ** 2 + (yi[1] - yc[1]) ** 2
+        gam = 1 + 2 * s / (a * b)
+        d = math.acosh(gam)
+        w = 1 / (1 + d * d)
+        if s == 0:
+            return w, (0.0, 0.0)
+        c = yc[0] ** 2 + yc[1] ** 2 - 2 * (yi[0] * yc[0] + yi[1] * yc[1]) + 1
+        den = a * b * math.sqrt(gam * gam - 1)
+        dd = (4 * (c * yi[0] / a - yc[0]) / den, 4 * (c * yi[1] / a - yc[1]) / den)
+        return w, (w * w * d * dd[0], w * w * d * dd[1])
+
+    F = np.zeros((n, 2))
+    Z = 0.0
+
+    def walk(node, i):
+        nonlocal Z
+        if not node.kids:
+            for j in node.pts:
+                if j != i:
+                    w, f = term(y[i], y[j])
+                    Z += w
+                    F[i] += f
+            return
+        if node.depth >= 1:
+            yc = midpoint(node.pts)
+            d = py_dist(y[i], yc)
+            if d > 0 and quad_diam(node) / d < theta:
+                w, f = term(y[i], yc)
+                Z += len(node.pts) * w
+                F[i] += len(node.pts) * np.array(f)
+                return
+        for key in sorted(node.kids):
+            walk(node.kids[key], i)
+
+    for i in range(n):
+        walk(root, i)
+    return F, Z
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.3, 0.6, 1.0])
+def test_bh_matches_pure_python_literal_algorithm(theta):
+    rng = np.random.default_rng(21)
+    y = np.concatenate([rng.normal(0, 0.25, (30, 2)), rng.normal([0.6, 0.2], 0.02, (10, 2))])
+    F, Z = py_bh([tuple(p) for p in y], theta)
+    bh = oracle.bh_grad(y, theta=theta)
+    assert bh["Z"] == pytest.approx(Z, rel=1e-12)
+    assert np.allclose(bh["frep"], F, rtol=1e-10, atol=1e-13 * np.abs(F).max())
+    if theta > 0.5:
+        assert bh["stats"][0] > 0  # some cells were summarised
+
+
+def _config1_small(n=1500):
+    w = inputs.make_config(1, seed=0, n=n)
+    y = inputs.spread_embedding(w.labels, 0, rho_hi=6.0)
+    return w, y
+
+
+def test_theta_zero_is_exact_and_error_falls_with_theta():
+    w, y = _config1_small()
+    ex = oracle.exact_grad(y, w.indptr, w.indices, w.values)
+    b0 = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=0.0)
+    assert np.linalg.norm(b0["g"] - ex["g"]) / np.linalg.norm(ex["g"]) < 1e-12
+    assert b0["Z"] == pytest.approx(ex["Z"], rel=1e-13)
+    errs = []
+    for th in [0.8, 0.5, 0.2, 0.1, 0.05]:
+        b = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=th)
+        errs.append(np.linalg.norm(b["g"] - ex["g"]) / np.linalg.norm(ex["g"]))
+    assert all(errs[k + 1] < errs[k] for k in range(len(errs) - 1)), errs
+    # theta = 0.5 error in the decade of Table GradientAndCostFunctionErrors
+    band = GOLDEN["bh_vs_exact_gradient_error_theta_0_5"]["values"]
+    assert min(band) / 10 < errs[1] < max(band) * 10, errs[1]
+
+
+def test_bh_cost_on_one_embedding():
+    # On one embedding the BH cost differs from the exact cost only through
+    # Z (C = sum p log p - sum p log w + log Z with sum p = 1), so
+    # C_bh - C_exact = log(Z_bh / Z_exact).  (The paper's cost-error column
+    # compares the exact costs of two separately optimised embeddings, which
+    # needs the full 1000-iteration runs and is not a per-Y quantity.)
+    w, y = _config1_small()
+    c_ex = oracle.kl(y, w.indptr, w.indices, w.values, theta=0.0)
+    c_bh = oracle.kl(y, w.indptr, w.indices, w.values, theta=0.5)
+    z_ex = oracle.exact_Z(y)
+    z_bh = oracle.bh_grad(y, theta=0.5)["Z"]
+    assert abs(z_bh - z_ex) / z_ex < 1e-2
+    assert c_bh - c_ex == pytest.approx(math.log(z_bh / z_ex), rel=1e-9, abs=1e-13)
+    assert abs(np.sum(w.values) - 1.0) < 1e-12
+
+
+def test_equal_area_rule_changes_tree_not_limits():
+    w, y = _config1_small(600)
+    t0 = oracle.tree_export(y, 0, 0)
+    t1 = oracle.tree_export(y, 1, 0)
+    assert len(t0["depth"]) != len(t1["depth"]) or not np.array_equal(t0["prefix"], t1["prefix"])
+    ex = oracle.exact_grad(y, w.indptr, w.indices, w.values)
+    for rule in (0, 1):
+        b0 = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=0.0, split_rule=rule)
+        assert np.allclose(b0["g"], ex["g"], rtol=1e-10, atol=1e-14)
