@@ -1,0 +1,377 @@
+"""Benchmark: Barnes-Hut hyperbolic t-SNE iterations per second at N = 1M.
+
+Workload: the single-cell-like configuration (N = 1,000,000 points in D = 50,
+200 clusters with Zipf sizes, log-normal features, P from exact kNN k = 90 at
+perplexity 30, float32 CSR), theta = 0.5, FP32-mixed pair forces.  A step is
+one full iteration of the hot path on the device: polar keys, radix sort,
+quadtree build, tree walk (repulsion + Z), attractive sum, Z reduction and
+the Riemannian update (non-exaggerated phase: exaggeration 1, momentum 0.8,
+lr = N / 12000).  The embedding starts from a synthetic spread state
+(clusters across the disk, some points within 1e-4 of the rim).
+
+Printed (one JSON line on rank 0): iterations/s of the FP32-mixed path, the
+all-FP64 GPU path for comparison, the FP32-mixed gradient's relative error
+against the FP64 oracle on 10,000 sampled rows, the tree walk's roofline,
+the end-to-end rate through the C ABI with host buffers, and the oracle's
+own rate on this host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BH grad iters/s at N=1M, FP32-mixed vs FP64 GPU, at <=1e-3 grad rel err"
+UNIT = "iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--fp64-steps", type=int, default=0, help="0: steps // 10 (at least 3)")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error gate / CPU baseline")
+    ap.add_argument("--sample-rows", type=int, default=10000)
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (independent replicas; no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def workload(args, device):
+    from paper_2401_13708_gb300 import inputs
+    t0 = time.time()
+    w = inputs.make_config(5, seed=args.seed, device=device, n=args.n)
+    y = inputs.spread_embedding(w.labels, args.seed)
+    return w, y, time.time() - t0
+
+
+def oracle_pass(w, y, theta, rows):
+    """One oracle BH pass: full tree + all n walks (for Z) + gradient rows."""
+    import oracle
+    cores = oracle.set_threads(0)
+    t0 = time.time()
+    ref = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=theta, exag=1.0, rows=rows)
+    return ref, time.time() - t0, cores
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    w, y, _ = workload(args, "cuda" if _cuda() else "cpu")
+    cores = oracle.set_threads(0)
+    n = w.n
+    rows_per_step = min(n, 4000)
+    rng = np.random.default_rng(args.seed + 1)
+    t0 = time.time()
+    oracle.bh_rows(y, None, None, None, args.theta, 1.0, 1.0, np.zeros(0, np.int64))
+    t_tree = time.time() - t0
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = rng.choice(n, size=rows_per_step, replace=False)
+        t0 = time.time()
+        oracle.bh_rows(y, w.indptr, w.indices, w.values, args.theta, 1.0, 1.0, rows)
+        dt = time.time() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    t_s = float(np.mean(times))
+    t_full = t_tree + (n / rows_per_step) * max(t_s - t_tree, 1e-9)
+    value = 1.0 / t_full
+    sample = (f"per step: oracle tree build over all {n} points + BH walk and attraction for {rows_per_step} "
+              f"random rows; iteration time extrapolated as t_tree + (N/rows)(t_step - t_tree), "
+              f"t_tree={t_tree:.2f}s t_step={t_s:.2f}s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"single-cell-like N={n} D=50, kNN k=90 perplexity 30, theta={args.theta}",
+                       "n": n, "nnz": w.nnz, "theta": args.theta},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+# Algorithmic FP32 operations of the tree walk (counted from the source
+# expressions of walk_f32_kernel / pair_terms_f32, an FMA counting 2):
+#   criterion per active lane at an internal cell: hi/lo difference (6),
+#     |Delta|^2 (3), delta (2), compare (1)                       -> 12
+#   pair term per interaction: clamp (1), delta (delta + 2) (2), sqrt (1),
+#     log1p (1), 1 + d^2 (2), rcp (1), w (1), rep (2), coefficient (2),
+#     accumulation (4 FMA = 8)                                    -> 21
+# A leaf interaction also forms Delta, s and delta (12).
+FLOPS_CRITERION = 12
+FLOPS_PAIR = 21
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2401_13708_gb300 import HyperbolicTSNE
+
+    dev = f"cuda:{local}"
+    w, y, t_gen = workload(args, dev)
+    n = w.n
+    lr = n / 12000.0
+    theta = args.theta
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(local)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+
+    # ---- FP32-mixed -----------------------------------------------------
+    t = HyperbolicTSNE(precision="fp32", device=local)
+    t.set_P(w.indptr, w.indices, w.values)
+    t.set_Y(y)
+    g32, z32 = t.grad(theta, 1.0)            # gradient at the start state (error gate)
+    t.set_counters(True)
+    t.grad(theta, 1.0)
+    cnt = t.get_counters()
+    t.set_counters(False)
+    acc, pairs, visits, queries = [int(v) for v in cnt[:4]]
+    t.step(args.warmup, theta, 1.0, lr, 0.8)
+    t.set_profiling(True)
+    t.get_profile()
+    launches0 = int(t.get_counters()[4])
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        t.step(args.steps, theta, 1.0, lr, 0.8)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    launches = int(t.get_counters()[4]) - launches0
+    prof, piters = t.get_profile()
+    t.set_profiling(False)
+    clocks = clk.summary()
+    ms_per_step = ms / args.steps
+    value = args.steps * world / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (tree walk) --------------------
+    walk_ms = prof["walk"] / max(piters, 1)
+    lane_visits = visits * 32  # upper bound of criterion evaluations: every lane of each warp visit
+    flops = acc * FLOPS_PAIR + pairs * (FLOPS_PAIR + FLOPS_CRITERION) + lane_visits * FLOPS_CRITERION
+    sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    achieved = flops / (walk_ms * 1e-3) / 1e12
+    dominant = max(prof, key=prof.get)
+
+    # ---- FP64 GPU path ----------------------------------------------------
+    k64 = args.fp64_steps or max(3, args.steps // 10)
+    t64 = HyperbolicTSNE(precision="fp64", device=local)
+    t64.set_P(w.indptr, w.indices, w.values)
+    t64.set_Y(y)
+    t64.step(1, theta, 1.0, lr, 0.8)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t64.step(k64, theta, 1.0, lr, 0.8)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(e0.elapsed_time(e1), world)
+    value64 = k64 * world / (ms64 / 1e3)
+    t64.close()
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    k_e2e = max(3, min(args.steps, 20))
+    yh = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
+    yo = torch.empty_like(yh).pin_memory()
+    t.step(1, theta, 1.0, lr, 0.8)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        t.set_Y(yh)
+        t.step(1, theta, 1.0, lr, 0.8)
+        t.get_Y(yo)
+    torch.cuda.synchronize()
+    barrier(world)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": k_e2e * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(yh.numel() * 8),
+           "d2h_bytes_per_step": int(yo.numel() * 8),
+           "call": "hts_set_Y(host) + hts_step(1) + hts_get_Y(host) per step, pinned host buffers"}
+    t.close()
+
+    # ---- oracle: error gate and CPU baseline (rank 0 only) ---------------
+    err = None
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_oracle:
+        rng = np.random.default_rng(args.seed + 2)
+        rows = np.sort(rng.choice(n, size=min(args.sample_rows, n), replace=False))
+        ref, t_or, cores = oracle_pass(w, y, theta, rows)
+        err = float(np.linalg.norm(g32[rows] - ref["g"]) / np.linalg.norm(ref["g"]))
+        z_err = abs(z32 - ref["Z"]) / ref["Z"]
+        cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"one FP64 oracle pass at N={n}: literal-insertion tree, BH walks of all {n} points "
+                          f"(for Z) and gradient rows for {len(rows)} sampled points; {t_or:.1f} s"),
+               "z_rel_err": z_err}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"single-cell-like N={n} D=50 (200 Zipf clusters, log-normal), kNN k=90 perplexity "
+                               f"30, FP32 CSR, theta={theta}, FP32-mixed", "n": n, "nnz": int(w.nnz),
+                   "theta": theta, "precision": "fp32_mixed", "y_state": "synthetic spread (mid-run-like)",
+                   "l2": "inputs larger than L2 (CSR ~%.2f GB)" % (w.nnz * 8 / 1e9),
+                   "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
+        "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                     "fp32_mixed_speedup": value / value64},
+        "grad_rel_err": err,
+        "phase_ms_per_step": {k: v / max(piters, 1) for k, v in prof.items()},
+        "walk_counters": {"accepted_cells": acc, "leaf_pairs": pairs, "warp_node_visits": visits,
+                          "queries": queries,
+                          "interactions_per_point": (acc + pairs) / max(queries, 1)},
+        "roofline": {"kernel": "walk_f32_kernel (BH tree walk)", "bound": "alu", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "dominant_phase": dominant,
+                     "peak_basis": "FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (sampled SM clock)" % (
+                         props.multi_processor_count, sm_mhz)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

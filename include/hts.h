@@ -1,0 +1,211 @@
+/*
+ * hts.h -- C ABI of libhts: the per-iteration gradient of hyperbolic t-SNE
+ * ("Accelerating hyperbolic t-SNE", arXiv 2401.13708) on one NVIDIA GB300.
+ *
+ * One context holds one embedding problem on one device: the sparse
+ * symmetric affinity matrix P (CSR), the embedding Y in the Poincare disk
+ * (n x 2, float64 master copy), the optimiser state (velocity, gains) and
+ * all device work buffers.  Every iteration runs on the device:
+ *
+ *   polar keys -> radix sort -> polar-quadtree build (Sec. 4.1)
+ *   -> attractive sum over P      (first sum of Eq. KlGradientHyperbolicSplit)
+ *   -> Barnes-Hut repulsion + Z   (second sum, Eq. CellApproximation, Sec. 4.2)
+ *   -> gradient and Riemannian step (Eq. PoincareMetric rescale, exp map,
+ *      Eq. HyperbolicProjection; momentum / exaggeration of Sec. 5.1)
+ *
+ * Conventions
+ *   - Return value: HTS_OK (0) or a negative HTS_E* code.  No C++ exception
+ *     or process exit crosses this boundary.  hts_last_error() gives a
+ *     human-readable message for the last failing call on a context.
+ *   - Ownership: inputs are copied into the context; the caller keeps its
+ *     buffers and may free them after the call returns.  Outputs are written
+ *     into caller buffers.  `where` says whether a pointer is host memory
+ *     (HTS_HOST) or device memory of the context's device (HTS_DEVICE).
+ *     Host buffers may be pageable or pinned.
+ *   - Streams: all work is queued on the stream given in hts_config (NULL =
+ *     the legacy default stream).  Calls that return data to the host
+ *     (host outputs, hts_kl, Z_out) synchronise that stream before returning;
+ *     device outputs are ready in stream order.
+ *   - Layout: y and gradients are n x 2 row-major float64 (x0, y0, x1, y1, ...).
+ *     CSR: indptr int64[n+1] (indptr[0] = 0, non-decreasing, indptr[n] = nnz),
+ *     indices int32[nnz] in [0, n), no diagonal entries; values float32 or
+ *     float64[nnz], finite and >= 0.  P is used as given (the caller
+ *     symmetrises and normalises it, Eq. HighDimensionalProbability).
+ *   - Threads: a context is not thread-safe; use one context per thread.
+ *   - theta == 0 means "no approximation" (Sec. 5.2.3): the exact O(n^2)
+ *     repulsion kernel replaces the tree walk.
+ */
+#ifndef HTS_H
+#define HTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HTS_API __attribute__((visibility("default")))
+#else
+#define HTS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define HTS_OK 0
+#define HTS_EINVAL (-1)   /* invalid argument: NULL pointer, unknown enum, bad theta/lr */
+#define HTS_ESHAPE (-2)   /* inconsistent sizes: n mismatch between P and Y, malformed CSR */
+#define HTS_ENOTSET (-3)  /* P or Y has not been set on this context */
+#define HTS_EDOMAIN (-4)  /* a point with |y| >= 1 or a non-finite coordinate/value */
+#define HTS_ECUDA (-5)    /* a CUDA runtime call failed (message has the CUDA error) */
+#define HTS_EOOM (-6)     /* device allocation failed */
+#define HTS_ENUMERIC (-7) /* device check tripped: non-finite gradient/position or tree overflow */
+
+/* ---- enums ------------------------------------------------------------ */
+#define HTS_FP64 0        /* every step in float64 */
+#define HTS_FP32_MIXED 1  /* pair forces in float32 (hi/lo point pairs, conformal
+                             factors from float64); Z, sums and the step in float64 */
+
+#define HTS_EQUAL_LENGTH 0 /* radial split at (max_r + min_r)/2, Eq. EqualEmbeddingLengthsSplitting */
+#define HTS_EQUAL_AREA 1   /* radial split at acosh((cosh max + cosh min)/2), Eq. EqualAreaSplitting */
+
+#define HTS_EXACT_KL 0     /* gradient 4 sum (p - q) w d dd/dy: the derivative of KL */
+#define HTS_PAPER_EQ 1     /* the form printed in Eq. KLGradientHyperbolic (without d) */
+
+#define HTS_HOST 0
+#define HTS_DEVICE 1
+
+#define HTS_F32 0
+#define HTS_F64 1
+
+#define HTS_TREE_LEVELS 29 /* depth cap of the polar quadtree (29 radial + 29 angular key bits) */
+
+typedef struct hts_ctx hts_ctx;
+
+typedef struct {
+    int precision;   /* HTS_FP64 | HTS_FP32_MIXED (default HTS_FP32_MIXED) */
+    int split_rule;  /* HTS_EQUAL_LENGTH (default) | HTS_EQUAL_AREA */
+    int grad_form;   /* HTS_EXACT_KL (default) | HTS_PAPER_EQ */
+    int metric_pow;  /* step rescale lambda^-metric_pow: 1 (default, "product of lambda^-1
+                        with the variation", Sec. 4.2) or 2 (Riemannian gradient) */
+    double eps;      /* projection margin of Eq. HyperbolicProjection: points that reach
+                        |y| >= 1 - eps/2 are put back at radius 1 - eps (default 1e-5) */
+    int use_gains;   /* per-coordinate gains (Sec. 5.1): +0.2 on sign disagreement of
+                        gradient and velocity, *0.8 otherwise, floor 0.01 (default 0) */
+    int device;      /* CUDA device ordinal (default 0) */
+    void *stream;    /* cudaStream_t to queue work on (default NULL) */
+} hts_config;
+
+/* Fill *cfg with the defaults listed above.  Never fails. */
+HTS_API void hts_default_config(hts_config *cfg);
+
+/* Create a context on cfg->device.  *out receives the handle (NULL on error).
+ * Allocates only host memory; device buffers are allocated by hts_set_P /
+ * hts_set_Y.  Errors: HTS_EINVAL (NULL out, bad enum, eps not in (0, 0.5)),
+ * HTS_ECUDA (device not usable). */
+HTS_API int hts_create(hts_ctx **out, const hts_config *cfg);
+
+/* Free every buffer of the context.  NULL is ignored. */
+HTS_API void hts_destroy(hts_ctx *ctx);
+
+/* Copy the affinity matrix P (n x n, CSR, see Conventions) into the context.
+ * dtype HTS_F32 | HTS_F64; in HTS_FP32_MIXED the values are kept as float32,
+ * in HTS_FP64 as float64.  Host inputs are validated (monotone indptr,
+ * indices in range and off-diagonal, finite non-negative values); device
+ * inputs are validated on the device.  Errors: HTS_EINVAL, HTS_ESHAPE (bad
+ * CSR or n differs from a Y already set), HTS_EDOMAIN (bad values),
+ * HTS_EOOM, HTS_ECUDA. */
+HTS_API int hts_set_P(hts_ctx *ctx, int64_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
+              const void *values, int dtype, int where);
+
+/* Copy the embedding Y (n x 2 float64) into the context and reset the
+ * velocity to 0 and the gains to 1.  Every point must satisfy |y| < 1 and be
+ * finite.  Errors: HTS_EINVAL, HTS_ESHAPE (n differs from P), HTS_EDOMAIN,
+ * HTS_EOOM, HTS_ECUDA. */
+HTS_API int hts_set_Y(hts_ctx *ctx, int64_t n, const double *y, int where);
+
+/* Run n_iter gradient-descent iterations (Sec. 5.1): each builds the tree
+ * from the current Y, computes g = 4 (exaggeration * F_attr - F_rep / Z) with
+ * the Barnes-Hut repulsion at `theta` (exact when theta == 0), and updates
+ *   v <- momentum * v - lr * gains * lambda^-metric_pow * g,
+ *   y <- proj(exp_y(v)).
+ * theta in [0, 1], exaggeration > 0, lr >= 0, momentum in [0, 1].
+ * Synchronises once at the end to read the device status word.
+ * Errors: HTS_ENOTSET, HTS_EINVAL, HTS_ENUMERIC, HTS_ECUDA. */
+HTS_API int hts_step(hts_ctx *ctx, int n_iter, double theta, double exaggeration, double lr, double momentum);
+
+/* Copy Y (n x 2 float64) out.  Errors: HTS_ENOTSET, HTS_EINVAL, HTS_ECUDA. */
+HTS_API int hts_get_Y(hts_ctx *ctx, double *y_out, int where);
+
+/* Euclidean gradient of KL at the current Y (no step, no rescale):
+ * g = 4 (exaggeration * F_attr - F_rep / Z), the split form of Eq.
+ * KlGradientHyperbolicSplit, with Z the Barnes-Hut (theta > 0) or exact
+ * (theta == 0) normalisation.  g_out (n x 2, may be NULL) in `where`
+ * memory; Z_out (host double, may be NULL).  Errors: HTS_ENOTSET,
+ * HTS_EINVAL, HTS_ENUMERIC, HTS_ECUDA. */
+HTS_API int hts_grad(hts_ctx *ctx, double theta, double exaggeration, double *g_out, double *Z_out, int where);
+
+/* KL(P || Q^H) at the current Y (Eq. KLDivergence with the hyperbolic q of
+ * Eq. LowDimensionalProbabilityHyperbolic), without exaggeration:
+ *   sum p log p - sum p log w + (sum p) log Z,
+ * Z from the tree (theta > 0) or exact (theta == 0).  *kl_out is a host
+ * double.  Errors: HTS_ENOTSET, HTS_EINVAL, HTS_ECUDA. */
+HTS_API int hts_kl(hts_ctx *ctx, double theta, double *kl_out);
+
+/* Message for the last failing call on ctx ("" if none; a static string
+ * when ctx is NULL).  Valid until the next call on ctx. */
+HTS_API const char *hts_last_error(const hts_ctx *ctx);
+
+/* ---- inspection and checkpointing ---------------------------------------- */
+
+/* Polar keys (Sec. 4.1, reading R5) of the current Y in point order:
+ * digit l (l = 1 most significant, bits 2(29-l)+1..2(29-l)) is
+ * 2 * radial_bit + angular_bit of the depth-l cell.  keys_out: uint64[n];
+ * bounds_out (host double[2], may be NULL): the root annulus [lo, hi] in the
+ * radial split coordinate.  Errors: HTS_ENOTSET, HTS_EINVAL, HTS_ECUDA. */
+HTS_API int hts_get_keys(hts_ctx *ctx, uint64_t *keys_out, double *bounds_out, int where);
+
+/* Build the tree for the current Y and export its nodes in pre-order
+ * (children in key order, chains of one-child cells collapsed to the
+ * deepest cell).  Call with cap = 0 (arrays may be NULL) to get the node
+ * count in *count_out; then with cap >= count.  Arrays are host memory:
+ * depth int32[cap], prefix uint64[cap] (top 2*depth key bits), count
+ * int64[cap] (N_cell), first int64[cap] (point index of a single-point leaf,
+ * smallest point index of a depth-29 bucket, -1 for internal cells), ycell
+ * double[2*cap] (Einstein midpoint of Eq. EinsteinMidpoint in disk
+ * coordinates, or the point), rcell double[cap] (longest internal distance
+ * of the cell, +inf for the root and for single-point leaves).
+ * Errors: HTS_ENOTSET, HTS_EINVAL (cap too small), HTS_ECUDA. */
+HTS_API int hts_get_tree(hts_ctx *ctx, int64_t cap, int64_t *count_out, int32_t *depth, uint64_t *prefix,
+                 int64_t *count, int64_t *first, double *ycell, double *rcell);
+
+/* Counters (host int64[5]): [0..3] of the last tree walk -- accepted cells,
+ * leaf pair interactions, warp node visits, query points -- filled only
+ * while hts_set_counters(ctx, 1) is on (the walk then runs a counting
+ * variant); [4] the number of CUDA kernels this context has launched. */
+HTS_API int hts_get_counters(hts_ctx *ctx, int64_t *out5);
+HTS_API int hts_set_counters(hts_ctx *ctx, int enable);
+
+/* Per-phase timing.  While profiling is on, hts_step records CUDA events on
+ * the context's stream at the phase boundaries of every iteration (up to
+ * 4096 per call).  hts_get_profile returns the accumulated milliseconds of
+ * the six phases -- keys, sort, tree build, tree walk (or exact kernel),
+ * attractive sum, Z + update -- and the number of iterations they cover,
+ * then resets them.  ms6: host double[6]. */
+HTS_API int hts_set_profiling(hts_ctx *ctx, int enable);
+HTS_API int hts_get_profile(hts_ctx *ctx, double *ms6, int64_t *iters);
+
+/* Optimiser state for checkpoint/resume: velocity and gains (n x 2 float64
+ * each) and the number of iterations run.  get: outputs may be NULL.
+ * set: NULL leaves a part unchanged.  Errors: HTS_ENOTSET, HTS_ECUDA. */
+HTS_API int hts_get_state(hts_ctx *ctx, double *vel, double *gains, int64_t *iters, int where);
+HTS_API int hts_set_state(hts_ctx *ctx, const double *vel, const double *gains, int64_t iters, int where);
+
+/* Number of points n and non-zeros nnz currently set (either may be NULL). */
+HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTS_H */

@@ -1,0 +1,728 @@
+// api.cu -- the C ABI of libhts (declared in include/hts.h).
+//
+// One iteration (hts_step) queues, on the context's stream:
+//   prep_points -> make_keys -> sort (8 passes) -> build_tree -> walk
+//   -> attract -> reduce_z -> update
+// or, for theta == 0, prep_points -> exact -> attract -> reduce_z -> update.
+// Nothing is allocated and nothing is copied to the host inside the loop;
+// the status word is read once after the last iteration.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hts_internal.cuh"
+
+using namespace hts;
+
+namespace {
+
+int fail(hts_ctx *c, int code, const char *msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(hts_ctx *c, cudaError_t e, const char *where)
+{
+    if (c) {
+        c->err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    }
+    return e == cudaErrorMemoryAllocation ? HTS_EOOM : HTS_ECUDA;
+}
+
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+#define LAUNCHED(what)                                       \
+    do {                                                     \
+        cudaError_t e_ = cudaGetLastError();                 \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+template <typename T>
+int dalloc(hts_ctx *c, T **p, size_t count)
+{
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(c, e, "cudaMalloc");
+    }
+    return HTS_OK;
+}
+
+template <typename T>
+void dfree(T **p)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+int set_device(hts_ctx *c)
+{
+    cudaError_t e = cudaSetDevice(c->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return HTS_OK;
+}
+
+// Check that a pointer given as HTS_DEVICE is device memory of our device.
+int check_device_ptr(hts_ctx *c, const void *p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, HTS_EINVAL, "pointer given as HTS_DEVICE is not CUDA memory");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(c, HTS_EINVAL, "pointer given as HTS_DEVICE is not device memory");
+    if (a.type == cudaMemoryTypeDevice && a.device != c->cfg.device)
+        return fail(c, HTS_EINVAL, "device pointer belongs to another device");
+    return HTS_OK;
+}
+
+int ensure_points(hts_ctx *c, int64_t n)
+{
+    if (n == c->cap_n && (c->pts32 || c->pts64)) return HTS_OK;
+    const size_t N = (size_t)std::max<int64_t>(n, 1);
+    int r;
+#define AL(ptr, cnt) \
+    if ((r = dalloc(c, &(ptr), (cnt))) != HTS_OK) return r
+    AL(c->y, N);
+    AL(c->vel, N);
+    AL(c->gains, N);
+    AL(c->fattr, N);
+    AL(c->frep, N);
+    AL(c->zi, N);
+    AL(c->radial, N);
+    if (c->cfg.precision == HTS_FP32_MIXED) {
+        AL(c->pts32, N);
+        AL(c->spts32, N);
+        AL(c->nodes32, 2 * N);
+    } else {
+        AL(c->pts64, N);
+        AL(c->spts64, N);
+        AL(c->nodes64, 2 * N);
+    }
+    AL(c->keys, N);
+    AL(c->keys_alt, N);
+    AL(c->idx, N);
+    AL(c->idx_alt, N);
+    AL(c->terms, 3 * N);
+    AL(c->bn_left, N);
+    AL(c->bn_right, N);
+    AL(c->bn_parent, N);
+    AL(c->leaf_parent, N);
+    AL(c->bn_lo, N);
+    AL(c->bn_hi, N);
+    AL(c->bn_pref, N);
+    AL(c->bn_flag, N);
+    AL(c->bn_quad, N);
+    AL(c->bn_sum, 6 * N);
+    AL(c->cnt, N + 1);
+    AL(c->pre, N + 1);
+    const int64_t tiles = ((int64_t)N + 4095) / 4096;
+    AL(c->sort_counts, (size_t)(256 * tiles));
+    c->scan_tmp_len = scan_tmp_size(std::max<int64_t>(256 * tiles, (int64_t)N + 1));
+    AL(c->scan_tmp, (size_t)c->scan_tmp_len);
+    AL(c->red_tmp, 3 * ((size_t)N * 32 / 256 + 2));
+#undef AL
+    c->n_nodes = c->pre + n;
+    c->cap_n = n;
+    return HTS_OK;
+}
+
+int read_status(hts_ctx *c, int *out)
+{
+    CK(cudaMemcpyAsync(c->h_pinned, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    memcpy(out, c->h_pinned, sizeof(int));
+    return HTS_OK;
+}
+
+int status_error(hts_ctx *c, int st)
+{
+    if (st & 64) return fail(c, HTS_EDOMAIN, "a point has |y| >= 1 or a non-finite coordinate");
+    if (st & (8 | 16)) return fail(c, HTS_ESHAPE, "malformed CSR (indptr, indices or diagonal entries)");
+    if (st & 32) return fail(c, HTS_EDOMAIN, "P has a negative or non-finite value");
+    if (st & 1) return fail(c, HTS_ENUMERIC, "non-finite gradient or position after a step");
+    if (st & (2 | 4)) return fail(c, HTS_ENUMERIC, "tree build/walk consistency check failed");
+    return HTS_OK;
+}
+
+constexpr int kPhases = 6;  // keys, sort, tree, walk/exact, attract, Z + update
+
+// Repulsion, attraction and Z for the current Y (results in frep, zi, fattr,
+// dscal[0]).  With `ev` (kPhases + 1 events) the phase boundaries are recorded.
+int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
+{
+#define MARK(k) \
+    if (ev) CK(cudaEventRecord(ev[k], c->stream))
+    MARK(0);
+    launch_prep_points(c);
+    LAUNCHED("prep_points");
+    if (theta == 0.0) {
+        MARK(1);
+        MARK(2);
+        MARK(3);
+        launch_exact(c);
+        LAUNCHED("exact");
+    } else {
+        launch_make_keys(c);
+        LAUNCHED("make_keys");
+        MARK(1);
+        launch_sort_pairs(c);
+        LAUNCHED("sort");
+        MARK(2);
+        launch_build_tree(c, theta, nullptr);
+        LAUNCHED("build_tree");
+        MARK(3);
+        launch_walk(c);
+        LAUNCHED("walk");
+    }
+    MARK(4);
+    if (c->nnz > 0) {
+        launch_attract(c);
+        LAUNCHED("attract");
+    } else {
+        CK(cudaMemsetAsync(c->fattr, 0, sizeof(double2) * (size_t)c->n, c->stream));
+    }
+    MARK(5);
+    launch_reduce_z(c);
+    LAUNCHED("reduce_z");
+#undef MARK
+    return HTS_OK;
+}
+
+int ensure_events(hts_ctx *c, int slots)
+{
+    if (slots <= c->event_slots) return HTS_OK;
+    cudaEvent_t *ev = new cudaEvent_t[(size_t)slots * (kPhases + 1)];
+    for (int k = 0; k < c->event_slots * (kPhases + 1); ++k) ev[k] = c->events[k];
+    for (int k = c->event_slots * (kPhases + 1); k < slots * (kPhases + 1); ++k) CK(cudaEventCreate(&ev[k]));
+    delete[] c->events;
+    c->events = ev;
+    c->event_slots = slots;
+    return HTS_OK;
+}
+
+int ready(hts_ctx *c)
+{
+    if (!c) return HTS_EINVAL;
+    if (!c->have_P || !c->have_Y) return fail(c, HTS_ENOTSET, "P and Y must both be set");
+    if (c->n != c->cap_n) return fail(c, HTS_ESHAPE, "P and Y sizes differ");
+    int r = set_device(c);
+    if (r) return r;
+    c->err.clear();
+    return HTS_OK;
+}
+
+int check_theta(hts_ctx *c, double theta)
+{
+    if (!(theta >= 0.0 && theta <= 1.0)) return fail(c, HTS_EINVAL, "theta must be in [0, 1]");
+    return HTS_OK;
+}
+
+__global__ void convert_values_kernel(int64_t nnz, const void *in, int in_f64, void *out, int out_f64)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    double v = in_f64 ? ((const double *)in)[e] : (double)((const float *)in)[e];
+    if (out_f64) ((double *)out)[e] = v; else ((float *)out)[e] = (float)v;
+}
+
+__global__ void fill_state_kernel(int64_t n, double2 *vel, double2 *gains)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    vel[i] = make_double2(0.0, 0.0);
+    gains[i] = make_double2(1.0, 1.0);
+}
+
+}  // namespace
+
+extern "C" {
+
+void hts_default_config(hts_config *cfg)
+{
+    if (!cfg) return;
+    cfg->precision = HTS_FP32_MIXED;
+    cfg->split_rule = HTS_EQUAL_LENGTH;
+    cfg->grad_form = HTS_EXACT_KL;
+    cfg->metric_pow = 1;
+    cfg->eps = 1e-5;
+    cfg->use_gains = 0;
+    cfg->device = 0;
+    cfg->stream = nullptr;
+}
+
+int hts_create(hts_ctx **out, const hts_config *cfg)
+{
+    if (!out) return HTS_EINVAL;
+    *out = nullptr;
+    hts_config k;
+    if (cfg) k = *cfg; else hts_default_config(&k);
+    if ((k.precision != HTS_FP64 && k.precision != HTS_FP32_MIXED) ||
+        (k.split_rule != HTS_EQUAL_LENGTH && k.split_rule != HTS_EQUAL_AREA) ||
+        (k.grad_form != HTS_EXACT_KL && k.grad_form != HTS_PAPER_EQ) || (k.metric_pow != 1 && k.metric_pow != 2) ||
+        !(k.eps > 0.0 && k.eps < 0.5) || k.device < 0)
+        return HTS_EINVAL;
+    hts_ctx *c = new hts_ctx();
+    c->cfg = k;
+    c->stream = (cudaStream_t)k.stream;
+    int r = set_device(c);
+    if (r) {
+        delete c;
+        return r;
+    }
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, k.device);
+    if (e != cudaSuccess) {
+        delete c;
+        return HTS_ECUDA;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    if (dalloc(c, &c->minmax, 2) || dalloc(c, &c->dscal, 8) || dalloc(c, &c->status, 1) ||
+        dalloc(c, &c->counters, 4) || cudaMallocHost((void **)&c->h_pinned, 8 * sizeof(double)) != cudaSuccess) {
+        hts_destroy(c);
+        return HTS_EOOM;
+    }
+    cudaMemset(c->counters, 0, 4 * sizeof(unsigned long long));
+    cudaMemset(c->status, 0, sizeof(int));
+    *out = c;
+    return HTS_OK;
+}
+
+void hts_destroy(hts_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->cfg.device);
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    dfree(&c->indptr); dfree(&c->indices); dfree(&c->values);
+    dfree(&c->y); dfree(&c->vel); dfree(&c->gains); dfree(&c->fattr); dfree(&c->frep);
+    dfree(&c->zi); dfree(&c->radial); dfree(&c->pts32); dfree(&c->pts64);
+    dfree(&c->keys); dfree(&c->keys_alt); dfree(&c->idx); dfree(&c->idx_alt);
+    dfree(&c->spts32); dfree(&c->spts64); dfree(&c->terms);
+    dfree(&c->bn_left); dfree(&c->bn_right); dfree(&c->bn_parent); dfree(&c->leaf_parent);
+    dfree(&c->bn_lo); dfree(&c->bn_hi); dfree(&c->bn_pref); dfree(&c->bn_flag); dfree(&c->bn_quad);
+    dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
+    dfree(&c->sort_counts); dfree(&c->scan_tmp); dfree(&c->red_tmp); dfree(&c->minmax);
+    dfree(&c->dscal); dfree(&c->status); dfree(&c->counters);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    for (int k = 0; k < c->event_slots * (kPhases + 1); ++k) cudaEventDestroy(c->events[k]);
+    delete[] c->events;
+    delete c;
+}
+
+const char *hts_last_error(const hts_ctx *c)
+{
+    if (!c) return "no context";
+    return c->err.c_str();
+}
+
+int hts_set_P(hts_ctx *c, int64_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices, const void *values,
+              int dtype, int where)
+{
+    if (!c) return HTS_EINVAL;
+    c->err.clear();
+    if (n < 0 || n > (1 << 30) || nnz < 0 || nnz > ((int64_t)1 << 40) || !indptr ||
+        (nnz > 0 && (!indices || !values)) || (dtype != HTS_F32 && dtype != HTS_F64) ||
+        (where != HTS_HOST && where != HTS_DEVICE))
+        return fail(c, HTS_EINVAL, "hts_set_P: invalid argument");
+    if (c->have_Y && n != c->n) return fail(c, HTS_ESHAPE, "hts_set_P: n differs from the n of Y");
+    int r = set_device(c);
+    if (r) return r;
+    const int in_f64 = dtype == HTS_F64;
+    const int out_f64 = c->cfg.precision == HTS_FP64;
+    if (where == HTS_HOST) {
+        if (indptr[0] != 0 || indptr[n] != nnz) return fail(c, HTS_ESHAPE, "hts_set_P: indptr[0] != 0 or indptr[n] != nnz");
+        for (int64_t i = 0; i < n; ++i) {
+            if (indptr[i + 1] < indptr[i]) return fail(c, HTS_ESHAPE, "hts_set_P: indptr decreases");
+            for (int64_t e = indptr[i]; e < indptr[i + 1]; ++e) {
+                int32_t j = indices[e];
+                if (j < 0 || j >= n || j == i) return fail(c, HTS_ESHAPE, "hts_set_P: index out of range or diagonal");
+                double v = in_f64 ? ((const double *)values)[e] : (double)((const float *)values)[e];
+                if (!(v >= 0.0) || !isfinite(v)) return fail(c, HTS_EDOMAIN, "hts_set_P: negative or non-finite value");
+            }
+        }
+    } else {
+        if ((r = check_device_ptr(c, indptr))) return r;
+        if (nnz > 0 && ((r = check_device_ptr(c, indices)) || (r = check_device_ptr(c, values)))) return r;
+    }
+    if ((r = dalloc(c, &c->indptr, (size_t)n + 1))) return r;
+    if ((r = dalloc(c, &c->indices, (size_t)nnz))) return r;
+    if (out_f64) {
+        double *v = nullptr;
+        if ((r = dalloc(c, &v, (size_t)nnz))) return r;
+        dfree(&c->values);
+        c->values = v;
+    } else {
+        float *v = nullptr;
+        if ((r = dalloc(c, &v, (size_t)nnz))) return r;
+        dfree(&c->values);
+        c->values = v;
+    }
+    cudaMemcpyKind kind = where == HTS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(c->indptr, indptr, sizeof(int64_t) * (size_t)(n + 1), kind, c->stream));
+    if (nnz > 0) CK(cudaMemcpyAsync(c->indices, indices, sizeof(int32_t) * (size_t)nnz, kind, c->stream));
+    if (nnz > 0) {
+        if (in_f64 == out_f64) {
+            CK(cudaMemcpyAsync(c->values, values, (size_t)nnz * (in_f64 ? 8 : 4), kind, c->stream));
+        } else if (where == HTS_HOST) {
+            if (out_f64) {
+                std::vector<double> tmp((size_t)nnz);
+                for (int64_t e = 0; e < nnz; ++e) tmp[e] = ((const float *)values)[e];
+                CK(cudaMemcpy(c->values, tmp.data(), 8 * (size_t)nnz, cudaMemcpyHostToDevice));
+            } else {
+                std::vector<float> tmp((size_t)nnz);
+                for (int64_t e = 0; e < nnz; ++e) tmp[e] = (float)((const double *)values)[e];
+                CK(cudaMemcpy(c->values, tmp.data(), 4 * (size_t)nnz, cudaMemcpyHostToDevice));
+            }
+        } else {
+            convert_values_kernel<<<(unsigned)((nnz + 255) / 256), 256, 0, c->stream>>>(nnz, values, in_f64,
+                                                                                      c->values, out_f64);
+            LAUNCHED("convert_values");
+        }
+    }
+    if (where == HTS_DEVICE && n > 0) {
+        CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        launch_validate_csr(c, (int)n, nnz, c->indptr, c->indices, c->values, out_f64);
+        LAUNCHED("validate_csr");
+        int st = 0;
+        if ((r = read_status(c, &st))) return r;
+        if (st) {
+            c->have_P = false;
+            return status_error(c, st);
+        }
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->values_f64 = out_f64;
+    c->n = n;
+    c->nnz = nnz;
+    c->have_P = true;
+    return HTS_OK;
+}
+
+int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
+{
+    if (!c) return HTS_EINVAL;
+    c->err.clear();
+    if (n < 0 || n > (1 << 30) || (n > 0 && !y) || (where != HTS_HOST && where != HTS_DEVICE))
+        return fail(c, HTS_EINVAL, "hts_set_Y: invalid argument");
+    if (c->have_P && n != c->n) return fail(c, HTS_ESHAPE, "hts_set_Y: n differs from the n of P");
+    int r = set_device(c);
+    if (r) return r;
+    if (where == HTS_HOST) {
+        for (int64_t i = 0; i < n; ++i) {
+            double a = y[2 * i], b = y[2 * i + 1];
+            if (!isfinite(a) || !isfinite(b) || !(a * a + b * b < 1.0))
+                return fail(c, HTS_EDOMAIN, "hts_set_Y: a point has |y| >= 1 or a non-finite coordinate");
+        }
+    } else if (n > 0 && (r = check_device_ptr(c, y))) {
+        return r;
+    }
+    if ((r = ensure_points(c, n))) return r;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(c->y, y, sizeof(double2) * (size_t)n,
+                           where == HTS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+        fill_state_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->vel, c->gains);
+        LAUNCHED("fill_state");
+        if (where == HTS_DEVICE) {
+            CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+            c->n = n;
+            launch_check_y(c);
+            LAUNCHED("check_y");
+            int st = 0;
+            if ((r = read_status(c, &st))) return r;
+            if (st) {
+                c->have_Y = false;
+                return status_error(c, st);
+            }
+        }
+    }
+    c->n = n;
+    c->iters = 0;
+    c->have_Y = true;
+    return HTS_OK;
+}
+
+int hts_step(hts_ctx *c, int n_iter, double theta, double exaggeration, double lr, double momentum)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (n_iter < 0 || !(exaggeration > 0.0) || !(lr >= 0.0) || !(momentum >= 0.0 && momentum <= 1.0) ||
+        !isfinite(exaggeration) || !isfinite(lr))
+        return fail(c, HTS_EINVAL, "hts_step: invalid n_iter, exaggeration, lr or momentum");
+    if ((r = check_theta(c, theta))) return r;
+    if (c->n == 0 || n_iter == 0) return HTS_OK;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    const int prof = c->profiling ? std::min(n_iter, 4096) : 0;
+    if (prof && (r = ensure_events(c, prof))) return r;
+    for (int it = 0; it < n_iter; ++it) {
+        cudaEvent_t *ev = it < prof ? c->events + (size_t)it * (kPhases + 1) : nullptr;
+        if ((r = run_gradient(c, theta, ev))) return r;
+        launch_update(c, exaggeration, lr, momentum, nullptr, 1);
+        LAUNCHED("update");
+        if (ev) CK(cudaEventRecord(ev[kPhases], c->stream));
+    }
+    c->iters += n_iter;
+    int st = 0;
+    if ((r = read_status(c, &st))) return r;
+    for (int it = 0; it < prof; ++it) {
+        cudaEvent_t *ev = c->events + (size_t)it * (kPhases + 1);
+        for (int k = 0; k < kPhases; ++k) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            c->phase_ms[k] += ms;
+        }
+    }
+    c->phase_iters += prof;
+    return status_error(c, st);
+}
+
+int hts_get_Y(hts_ctx *c, double *y_out, int where)
+{
+    if (!c) return HTS_EINVAL;
+    if (!c->have_Y) return fail(c, HTS_ENOTSET, "Y is not set");
+    if (!y_out && c->n > 0) return fail(c, HTS_EINVAL, "hts_get_Y: NULL output");
+    int r = set_device(c);
+    if (r) return r;
+    if (c->n == 0) return HTS_OK;
+    if (where == HTS_DEVICE && (r = check_device_ptr(c, y_out))) return r;
+    CK(cudaMemcpyAsync(y_out, c->y, sizeof(double2) * (size_t)c->n,
+                       where == HTS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    if (where == HTS_HOST) CK(cudaStreamSynchronize(c->stream));
+    return HTS_OK;
+}
+
+int hts_grad(hts_ctx *c, double theta, double exaggeration, double *g_out, double *Z_out, int where)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!(exaggeration > 0.0) || !isfinite(exaggeration)) return fail(c, HTS_EINVAL, "hts_grad: bad exaggeration");
+    if ((r = check_theta(c, theta))) return r;
+    if (where != HTS_HOST && where != HTS_DEVICE) return fail(c, HTS_EINVAL, "hts_grad: bad where");
+    if (c->n == 0) {
+        if (Z_out) *Z_out = 0.0;
+        return HTS_OK;
+    }
+    if (g_out && where == HTS_DEVICE && (r = check_device_ptr(c, g_out))) return r;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    if ((r = run_gradient(c, theta))) return r;
+    // a host output is staged in the tree-build scratch `terms` (3n doubles)
+    double2 *dst = nullptr;
+    if (g_out) dst = where == HTS_DEVICE ? (double2 *)g_out : (double2 *)c->terms;
+    launch_update(c, exaggeration, 0.0, 0.0, dst, 0);
+    LAUNCHED("combine");
+    if (g_out && where == HTS_HOST)
+        CK(cudaMemcpyAsync(g_out, c->terms, sizeof(double2) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_pinned + 1, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int st = 0;
+    if ((r = read_status(c, &st))) return r;
+    if (Z_out) *Z_out = c->h_pinned[1];
+    return status_error(c, st);
+}
+
+int hts_kl(hts_ctx *c, double theta, double *kl_out)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!kl_out) return fail(c, HTS_EINVAL, "hts_kl: NULL output");
+    if ((r = check_theta(c, theta))) return r;
+    if (c->n == 0) {
+        *kl_out = 0.0;
+        return HTS_OK;
+    }
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    int64_t keep = c->nnz;
+    c->nnz = 0;  // Z only: skip the attractive sum
+    r = run_gradient(c, theta);
+    c->nnz = keep;
+    if (r) return r;
+    if (c->nnz > 0) {
+        launch_kl_terms(c);
+        LAUNCHED("kl_terms");
+    } else {
+        CK(cudaMemsetAsync(c->dscal + 1, 0, 3 * sizeof(double), c->stream));
+    }
+    CK(cudaMemcpyAsync(c->h_pinned + 2, c->dscal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int st = 0;
+    if ((r = read_status(c, &st))) return r;
+    if ((r = status_error(c, st))) return r;
+    double Z = c->h_pinned[2], plogp = c->h_pinned[3], plogw = c->h_pinned[4], sp = c->h_pinned[5];
+    *kl_out = plogp - plogw + (sp > 0.0 ? sp * log(Z) : 0.0);
+    return HTS_OK;
+}
+
+int hts_get_keys(hts_ctx *c, uint64_t *keys_out, double *bounds_out, int where)
+{
+    if (!c) return HTS_EINVAL;
+    if (!c->have_Y) return fail(c, HTS_ENOTSET, "Y is not set");
+    int r = set_device(c);
+    if (r) return r;
+    if (c->n == 0) return HTS_OK;
+    if (!keys_out) return fail(c, HTS_EINVAL, "hts_get_keys: NULL output");
+    if (where == HTS_DEVICE && (r = check_device_ptr(c, keys_out))) return r;
+    launch_prep_points(c);
+    LAUNCHED("prep_points");
+    launch_make_keys(c);
+    LAUNCHED("make_keys");
+    CK(cudaMemcpyAsync(keys_out, c->keys, sizeof(uint64_t) * (size_t)c->n,
+                       where == HTS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    unsigned long long mm[2];
+    CK(cudaMemcpyAsync(mm, c->minmax, sizeof(mm), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (bounds_out) {
+        memcpy(&bounds_out[0], &mm[0], 8);
+        memcpy(&bounds_out[1], &mm[1], 8);
+    }
+    return HTS_OK;
+}
+
+int hts_get_tree(hts_ctx *c, int64_t cap, int64_t *count_out, int32_t *depth, uint64_t *prefix, int64_t *count,
+                 int64_t *first, double *ycell, double *rcell)
+{
+    if (!c) return HTS_EINVAL;
+    if (!c->have_Y) return fail(c, HTS_ENOTSET, "Y is not set");
+    int r = set_device(c);
+    if (r) return r;
+    const int64_t n = c->n;
+    if (n == 0) {
+        if (count_out) *count_out = 0;
+        return HTS_OK;
+    }
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    const size_t M = 2 * (size_t)n;
+    TreeExport ex{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool want = cap > 0;
+    if (want) {
+        CK(cudaMalloc((void **)&ex.depth, M * sizeof(int32_t)));
+        CK(cudaMalloc((void **)&ex.prefix, M * sizeof(uint64_t)));
+        CK(cudaMalloc((void **)&ex.count, M * sizeof(int64_t)));
+        CK(cudaMalloc((void **)&ex.first, M * sizeof(int64_t)));
+        CK(cudaMalloc((void **)&ex.ycell, 2 * M * sizeof(double)));
+        CK(cudaMalloc((void **)&ex.rcell, M * sizeof(double)));
+    }
+    launch_prep_points(c);
+    launch_make_keys(c);
+    launch_sort_pairs(c);
+    launch_build_tree(c, 0.5, want ? &ex : nullptr);
+    LAUNCHED("tree export");
+    int m = 0;
+    CK(cudaMemcpyAsync(&m, c->n_nodes, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (m < 0 || m > (int64_t)M) {
+        if (want) {
+            cudaFree(ex.depth); cudaFree(ex.prefix); cudaFree(ex.count); cudaFree(ex.first);
+            cudaFree(ex.ycell); cudaFree(ex.rcell);
+        }
+        return fail(c, HTS_ENUMERIC, "hts_get_tree: node count out of range");
+    }
+    if (count_out) *count_out = m;
+    int st = 0;
+    if ((r = read_status(c, &st))) return r;
+    if (want) {
+        int rc = HTS_OK;
+        if (cap < m) {
+            rc = fail(c, HTS_EINVAL, "hts_get_tree: cap smaller than the node count");
+        } else {
+            if (depth) cudaMemcpy(depth, ex.depth, m * sizeof(int32_t), cudaMemcpyDeviceToHost);
+            if (prefix) cudaMemcpy(prefix, ex.prefix, m * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+            if (count) cudaMemcpy(count, ex.count, m * sizeof(int64_t), cudaMemcpyDeviceToHost);
+            if (first) cudaMemcpy(first, ex.first, m * sizeof(int64_t), cudaMemcpyDeviceToHost);
+            if (ycell) cudaMemcpy(ycell, ex.ycell, 2 * m * sizeof(double), cudaMemcpyDeviceToHost);
+            if (rcell) cudaMemcpy(rcell, ex.rcell, m * sizeof(double), cudaMemcpyDeviceToHost);
+        }
+        cudaFree(ex.depth); cudaFree(ex.prefix); cudaFree(ex.count); cudaFree(ex.first);
+        cudaFree(ex.ycell); cudaFree(ex.rcell);
+        if (rc) return rc;
+    }
+    return status_error(c, st);
+}
+
+int hts_set_counters(hts_ctx *c, int enable)
+{
+    if (!c) return HTS_EINVAL;
+    c->counters_on = enable ? 1 : 0;
+    return HTS_OK;
+}
+
+int hts_get_counters(hts_ctx *c, int64_t *out5)
+{
+    if (!c || !out5) return HTS_EINVAL;
+    int r = set_device(c);
+    if (r) return r;
+    unsigned long long v[4];
+    CK(cudaMemcpyAsync(v, c->counters, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 4; ++k) out5[k] = (int64_t)v[k];
+    out5[4] = c->launches;
+    return HTS_OK;
+}
+
+int hts_set_profiling(hts_ctx *c, int enable)
+{
+    if (!c) return HTS_EINVAL;
+    c->profiling = enable ? 1 : 0;
+    return HTS_OK;
+}
+
+int hts_get_profile(hts_ctx *c, double *ms6, int64_t *iters)
+{
+    if (!c || !ms6) return HTS_EINVAL;
+    for (int k = 0; k < kPhases; ++k) {
+        ms6[k] = c->phase_ms[k];
+        c->phase_ms[k] = 0.0;
+    }
+    if (iters) *iters = c->phase_iters;
+    c->phase_iters = 0;
+    return HTS_OK;
+}
+
+int hts_get_state(hts_ctx *c, double *vel, double *gains, int64_t *iters, int where)
+{
+    if (!c) return HTS_EINVAL;
+    if (!c->have_Y) return fail(c, HTS_ENOTSET, "Y is not set");
+    int r = set_device(c);
+    if (r) return r;
+    cudaMemcpyKind k = where == HTS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (vel && c->n) CK(cudaMemcpyAsync(vel, c->vel, sizeof(double2) * (size_t)c->n, k, c->stream));
+    if (gains && c->n) CK(cudaMemcpyAsync(gains, c->gains, sizeof(double2) * (size_t)c->n, k, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (iters) *iters = c->iters;
+    return HTS_OK;
+}
+
+int hts_set_state(hts_ctx *c, const double *vel, const double *gains, int64_t iters, int where)
+{
+    if (!c) return HTS_EINVAL;
+    if (!c->have_Y) return fail(c, HTS_ENOTSET, "Y is not set");
+    int r = set_device(c);
+    if (r) return r;
+    cudaMemcpyKind k = where == HTS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (vel && c->n) CK(cudaMemcpyAsync(c->vel, vel, sizeof(double2) * (size_t)c->n, k, c->stream));
+    if (gains && c->n) CK(cudaMemcpyAsync(c->gains, gains, sizeof(double2) * (size_t)c->n, k, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->iters = iters;
+    return HTS_OK;
+}
+
+int hts_get_sizes(const hts_ctx *c, int64_t *n, int64_t *nnz)
+{
+    if (!c) return HTS_EINVAL;
+    if (n) *n = c->n;
+    if (nnz) *nnz = c->nnz;
+    return HTS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,231 @@
+// attract.cu -- the attractive sum over P (first sum of Eq.
+// KlGradientHyperbolicSplit), the KL cost terms (Eq. KLDivergence) and
+// device-side validation of a CSR matrix.
+//
+// One warp per row of P: the 32 lanes read consecutive (index, value)
+// entries (coalesced 128-byte loads), gather the neighbours' 32-byte point
+// records (random, mostly L2 hits) and reduce three scalars by shuffles.
+// Per point: F_attr,i = 4 il_i (A_Delta + il_i A_s y_i) with
+//   A_Delta = sum_j p_ij (w d / t)_ij il_j Delta_ij,  A_s = same with s_ij.
+// Bytes per non-zero: 4 (index) + 4 or 8 (value) + 32 (gathered record).
+#include "hts_internal.cuh"
+
+namespace hts {
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int GF>
+__global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_t *__restrict__ indptr,
+                                                             const int32_t *__restrict__ indices,
+                                                             const float *__restrict__ vals,
+                                                             const PointF *__restrict__ pts, double2 *fattr)
+{
+    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const PointF q = pts[row];
+    const float twoil = 2.0f * q.il;
+    const int64_t e0 = indptr[row], e1 = indptr[row + 1];
+    float ax = 0.f, ay = 0.f, as = 0.f;
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const int j = __ldg(indices + e);
+        const float pv = __ldg(vals + e);
+        const PointF o = pts[j];
+        float dx = (q.xh - o.xh) + (q.xl - o.xl);
+        float dy = (q.yh - o.yh) + (q.yl - o.yl);
+        float s = fmaf(dx, dx, dy * dy);
+        PairF t = pair_terms_f32<GF>(s * twoil * o.il);
+        float k = pv * t.att * o.il;
+        ax = fmaf(k, dx, ax);
+        ay = fmaf(k, dy, ay);
+        as = fmaf(k, s, as);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        as += __shfl_xor_sync(0xffffffffu, as, o);
+    }
+    if (lane == 0) {
+        double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
+        double il = (double)q.il;
+        double asd = il * (double)as;
+        fattr[row] = make_double2(4.0 * il * ((double)ax + asd * x), 4.0 * il * ((double)ay + asd * y));
+    }
+}
+
+template <int GF>
+__global__ void __launch_bounds__(kBlock) attract_f64_kernel(int n, const int64_t *__restrict__ indptr,
+                                                             const int32_t *__restrict__ indices,
+                                                             const double *__restrict__ vals,
+                                                             const PointD *__restrict__ pts, double2 *fattr)
+{
+    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const PointD q = pts[row];
+    const double twoil = 2.0 * q.il;
+    const int64_t e0 = indptr[row], e1 = indptr[row + 1];
+    double ax = 0, ay = 0, as = 0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const int j = __ldg(indices + e);
+        const double pv = __ldg(vals + e);
+        const PointD o = pts[j];
+        double dx = q.x - o.x, dy = q.y - o.y;
+        double s = fma(dx, dx, dy * dy);
+        PairD t = pair_terms_f64<GF>(s * twoil * o.il);
+        double k = pv * t.att * o.il;
+        ax = fma(k, dx, ax);
+        ay = fma(k, dy, ay);
+        as = fma(k, s, as);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        as += __shfl_xor_sync(0xffffffffu, as, o);
+    }
+    if (lane == 0) {
+        double asd = q.il * as;
+        fattr[row] = make_double2(4.0 * q.il * (ax + asd * q.x), 4.0 * q.il * (ay + asd * q.y));
+    }
+}
+
+// KL terms in float64 from the float64 positions: per block partial sums of
+// p log p, p log w = -p log1p(d^2) and p, combined in fixed order later.
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) kl_terms_kernel(int n, const int64_t *__restrict__ indptr,
+                                                          const int32_t *__restrict__ indices,
+                                                          const VT *__restrict__ vals, const double2 *__restrict__ y,
+                                                          double *partial)
+{
+    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    double a = 0, b = 0, sp = 0;
+    if (row < n) {
+        const double2 q = y[row];
+        const double ai = 1.0 - (q.x * q.x + q.y * q.y);
+        for (int64_t e = indptr[row] + lane; e < indptr[row + 1]; e += 32) {
+            const double pv = (double)vals[e];
+            if (!(pv > 0.0)) continue;
+            const double2 o = y[indices[e]];
+            double dx = q.x - o.x, dy = q.y - o.y;
+            double bj = 1.0 - (o.x * o.x + o.y * o.y);
+            double delta = 2.0 * (dx * dx + dy * dy) / (ai * bj);
+            double d = log1p(delta + sqrt(delta * (delta + 2.0)));
+            a += pv * log(pv);
+            b -= pv * log1p(d * d);
+            sp += pv;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    }
+    __shared__ double sh[3][kBlock / 32];
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][w] = a;
+        sh[1][w] = b;
+        sh[2][w] = sp;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0;
+        for (int k = 0; k < kBlock / 32; ++k) t += sh[threadIdx.x][k];
+        partial[3 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+__global__ void sum_partials_kernel(int blocks, const double *__restrict__ partial, double *out3)
+{
+    __shared__ double sh[3][256];
+    double a = 0, b = 0, c = 0;
+    for (int k = threadIdx.x; k < blocks; k += 256) {
+        a += partial[3 * k];
+        b += partial[3 * k + 1];
+        c += partial[3 * k + 2];
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    sh[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out3[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// status bits: 8 bad indptr, 16 bad index / diagonal, 32 bad value
+template <typename VT>
+__global__ void validate_csr_kernel(int n, int64_t nnz, const int64_t *__restrict__ indptr,
+                                    const int32_t *__restrict__ indices, const VT *__restrict__ vals, int *status)
+{
+    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int64_t e0 = indptr[row], e1 = indptr[row + 1];
+    if (lane == 0) {
+        if ((row == 0 && e0 != 0) || e1 < e0 || (row == n - 1 && e1 != nnz) || e1 > nnz || e0 < 0)
+            atomicOr(status, 8);
+    }
+    if (e1 < e0 || e0 < 0 || e1 > nnz) return;
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        int j = indices[e];
+        if (j < 0 || j >= n || j == row) atomicOr(status, 16);
+        double v = (double)vals[e];
+        if (!(v >= 0.0) || !isfinite(v)) atomicOr(status, 32);
+    }
+}
+
+}  // namespace
+
+void launch_attract(hts_ctx *c)
+{
+    const int n = (int)c->n;
+    const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
+    c->launches += 1;
+    if (c->cfg.precision == HTS_FP32_MIXED) {
+        const float *v = (const float *)c->values;
+        if (c->cfg.grad_form == HTS_EXACT_KL)
+            attract_f32_kernel<0><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32, c->fattr);
+        else
+            attract_f32_kernel<1><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32, c->fattr);
+    } else {
+        const double *v = (const double *)c->values;
+        if (c->cfg.grad_form == HTS_EXACT_KL)
+            attract_f64_kernel<0><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts64, c->fattr);
+        else
+            attract_f64_kernel<1><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts64, c->fattr);
+    }
+}
+
+void launch_kl_terms(hts_ctx *c)
+{
+    const int n = (int)c->n;
+    const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
+    if (c->values_f64)
+        kl_terms_kernel<double><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices,
+                                                                  (const double *)c->values, c->y, c->red_tmp);
+    else
+        kl_terms_kernel<float><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, (const float *)c->values,
+                                                                 c->y, c->red_tmp);
+    sum_partials_kernel<<<1, 256, 0, c->stream>>>(blocks, c->red_tmp, c->dscal + 1);
+    c->launches += 2;
+}
+
+void launch_validate_csr(hts_ctx *c, int n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
+                         const void *values, int f64)
+{
+    const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
+    if (f64)
+        validate_csr_kernel<double><<<blocks, kBlock, 0, c->stream>>>(n, nnz, indptr, indices,
+                                                                       (const double *)values, c->status);
+    else
+        validate_csr_kernel<float><<<blocks, kBlock, 0, c->stream>>>(n, nnz, indptr, indices, (const float *)values,
+                                                                     c->status);
+}
+
+}  // namespace hts

@@ -1,0 +1,257 @@
+// hts_internal.cuh -- data layout, context and device helpers of libhts.
+//
+// Every array lives in HBM of one GB300 and is allocated once per problem
+// size (hts_set_P / hts_set_Y); an iteration allocates nothing.
+//
+// Per point (n), original order:  y, vel, gains (double2), fattr, frep
+//   (double2), zi (double), pts32 / pts64 (32-byte point records: position
+//   as float hi/lo pairs or double, and il = 1 / (1 - |y|^2) taken from
+//   float64), radial (double, split coordinate of the point).
+// Per point, key order:  keys / idx (uint64 / uint32, sort ping-pong),
+//   spts32 / spts64 (gathered records), terms (Einstein terms, 3 doubles).
+// Binary radix tree over the sorted keys (n - 1 internal nodes): children,
+//   parents, ranges, prefix lengths, arrival flags, double-double sums.
+// Polar quadtree (<= 2n - 1 nodes), pre-order with skip indices:
+//   NodeF (32 B) or NodeD (48 B).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hts.h"
+
+namespace hts {
+
+constexpr int kLevels = HTS_TREE_LEVELS;  // 29 levels: 58 key bits
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Point record, float32 mode: position as hi + lo float pairs (the pair
+// carries ~48 bits, enough to form |y_i - y_j| of nearby points near the
+// rim without cancellation) and il = 1 / (1 - |y|^2) rounded from float64.
+struct __align__(16) PointF {
+    float xh, yh, xl, yl;
+    float il, pad0, pad1, pad2;
+};
+
+// Point record, float64 mode.
+struct __align__(16) PointD {
+    double x, y, il, pad;
+};
+
+// Tree node, float32 mode (one 32-byte sector).
+//   count >= 2 : internal cell; (xh, yh, xl, yl) Einstein midpoint, il of the
+//                midpoint, thr = cosh(r_cell / theta) - 1 (accept iff the
+//                pair's delta = cosh(d) - 1 exceeds it), skip = pre-order
+//                index after the subtree.
+//   count == 1 : single-point leaf; the point itself, thr holds the point's
+//                sorted position (int bits), skip = index + 1.
+//   count <  0 : depth-29 bucket of -count points; thr holds the sorted
+//                position of its first point (int bits).
+struct __align__(16) NodeF {
+    float xh, yh, xl, yl;
+    float il, thr;
+    int count, skip;
+};
+
+// Tree node, float64 mode (same meaning; pos = sorted position for leaves
+// and buckets).
+struct __align__(16) NodeD {
+    double x, y, il, thr;
+    int count, skip, pos, pad;
+};
+
+struct TreeExport {  // optional host-visible copy of the tree (device arrays)
+    int32_t *depth;
+    uint64_t *prefix;
+    int64_t *count, *first;
+    double *ycell, *rcell;
+};
+
+}  // namespace hts
+
+struct hts_ctx {
+    hts_config cfg;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+
+    int64_t n = 0, nnz = 0;
+    bool have_P = false, have_Y = false;
+    int64_t cap_n = 0, cap_nnz = 0;  // allocated capacities
+    int values_f64 = 0;             // stored dtype of P values
+    int64_t iters = 0;
+    int counters_on = 0;
+
+    // CSR
+    int64_t *indptr = nullptr;
+    int32_t *indices = nullptr;
+    void *values = nullptr;
+
+    // per point, original order
+    double2 *y = nullptr, *vel = nullptr, *gains = nullptr, *fattr = nullptr, *frep = nullptr;
+    double *zi = nullptr, *radial = nullptr;
+    hts::PointF *pts32 = nullptr;
+    hts::PointD *pts64 = nullptr;
+
+    // per point, key order
+    uint64_t *keys = nullptr, *keys_alt = nullptr;
+    uint32_t *idx = nullptr, *idx_alt = nullptr;
+    hts::PointF *spts32 = nullptr;
+    hts::PointD *spts64 = nullptr;
+    double *terms = nullptr;  // 3 per point
+
+    // binary radix tree
+    int *bn_left = nullptr, *bn_right = nullptr, *bn_parent = nullptr, *leaf_parent = nullptr;
+    int *bn_lo = nullptr, *bn_hi = nullptr, *bn_pref = nullptr, *bn_flag = nullptr, *bn_quad = nullptr;
+    double *bn_sum = nullptr;  // 6 per node (double-double S_gamma, S_ux, S_uy)
+    int *cnt = nullptr, *pre = nullptr;  // n + 1 each
+
+    // quadtree
+    hts::NodeF *nodes32 = nullptr;
+    hts::NodeD *nodes64 = nullptr;
+
+    // scratch
+    uint32_t *sort_counts = nullptr;  // 256 * tiles
+    int *scan_tmp = nullptr;
+    int64_t scan_tmp_len = 0;
+    double *red_tmp = nullptr;        // reduction partials
+    unsigned long long *minmax = nullptr;  // [0] min bits, [1] max bits
+    double *dscal = nullptr;          // [0] Z, [1] sum p log p, [2] sum p log w, [3] sum p
+    int *status = nullptr;
+    unsigned long long *counters = nullptr;  // 4
+    int *n_nodes = nullptr;          // device scalar: number of tree nodes
+    double *h_pinned = nullptr;      // 8 doubles of pinned host scratch
+
+    // instrumentation
+    int64_t launches = 0;            // kernels launched since creation
+    int profiling = 0;               // record phase events every iteration
+    cudaEvent_t *events = nullptr;   // kPhases + 1 per iteration slot
+    int event_slots = 0;
+    double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t phase_iters = 0;
+};
+
+namespace hts {
+
+// ---- host launchers (one translation unit each) -------------------------
+// keys.cu
+void launch_prep_points(hts_ctx *c);
+void launch_make_keys(hts_ctx *c);
+// sort.cu
+void launch_sort_pairs(hts_ctx *c);
+int scan_exclusive(const int *in, int *out, int64_t len, int *tmp, cudaStream_t s);  // returns kernels launched
+int64_t scan_tmp_size(int64_t len);
+// tree.cu
+void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex);
+// traverse.cu
+void launch_walk(hts_ctx *c);
+void launch_exact(hts_ctx *c);
+// attract.cu
+void launch_attract(hts_ctx *c);
+void launch_kl_terms(hts_ctx *c);
+void launch_validate_csr(hts_ctx *c, int n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
+                         const void *values, int f64);
+// update.cu
+void launch_reduce_z(hts_ctx *c);
+void launch_update(hts_ctx *c, double exag, double lr, double mom, double2 *g_out, int do_step);
+void launch_check_y(hts_ctx *c);
+
+}  // namespace hts
+
+// ---- device helpers ------------------------------------------------------
+#ifdef __CUDACC__
+namespace hts {
+
+// Pair term of the repulsive and attractive sums for y_i and a point or
+// cell midpoint c, written in terms of delta = cosh(d) - 1 =
+// 2 |y_i - c|^2 il_i il_c (Eq. PoincareDistance).  With t = sinh(d) =
+// sqrt(delta (delta + 2)), d = log1p(delta + t), w = 1 / (1 + d^2)
+// and r1 = 1 / (t (1 + d^2)):
+//   w          = t r1
+//   w^2 d / t  = w d r1          (repulsion, exact KL form)
+//   w d / t    = d r1            (attraction, exact KL form)
+// and Eq. PoincareDistanceDerivative reads
+//   dd/dy_i = 4 il_i il_c (Delta + s il_i y_i) / t,   s = |Delta|^2,
+// so every pair adds a scalar times (Delta, s); the common 4 il_i factor
+// and the il_i s y_i term are applied once per point at the end.
+// delta is clamped below by a tiny positive number so that coincident
+// points give w = 1 and zero force (the limit of w^2 d dd/dy as d -> 0).
+struct PairF {
+    float w, rep, att;  // w, w^2 d / t (or w^2 / t), w d / t (or w / t)
+};
+
+template <int GF>
+__device__ __forceinline__ PairF pair_terms_f32(float delta)
+{
+    delta = fmaxf(delta, 1e-30f);
+    float t = sqrtf(delta * (delta + 2.0f));
+    float d = log1pf(delta + t);
+    float u = fmaf(d, d, 1.0f);
+    float r1 = __frcp_rn(t * u);
+    PairF p;
+    p.w = t * r1;
+    if (GF == 0) {
+        p.att = d * r1;
+        p.rep = p.w * p.att;
+    } else {
+        p.att = r1;
+        p.rep = p.w * r1;
+    }
+    return p;
+}
+
+struct PairD {
+    double w, rep, att;
+};
+
+template <int GF>
+__device__ __forceinline__ PairD pair_terms_f64(double delta)
+{
+    delta = fmax(delta, 1e-300);
+    double t = sqrt(delta * (delta + 2.0));
+    double d = log1p(delta + t);
+    double u = fma(d, d, 1.0);
+    double r1 = 1.0 / (t * u);
+    PairD p;
+    p.w = t * r1;
+    if (GF == 0) {
+        p.att = d * r1;
+        p.rep = p.w * p.att;
+    } else {
+        p.att = r1;
+        p.rep = p.w * r1;
+    }
+    return p;
+}
+
+// Double-double addition (Knuth's TwoSum followed by a fast renormalisation),
+// with explicitly rounded operations so the compiler cannot fuse or reorder.
+struct DD {
+    double hi, lo;
+};
+
+__device__ __forceinline__ DD dd_add(DD a, DD b)
+{
+    double s = __dadd_rn(a.hi, b.hi);
+    double v = __dsub_rn(s, a.hi);
+    double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, v)), __dsub_rn(b.hi, v));
+    e = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
+    double hi = __dadd_rn(s, e);
+    double lo = __dsub_rn(e, __dsub_rn(hi, s));
+    return DD{hi, lo};
+}
+
+// Quadtree level of a binary-radix-tree node from its common-prefix length
+// (Karras' delta: clz of the key xor, or 64 + clz of the index xor for equal
+// keys).  Keys occupy the low 58 bits, so distinct keys have delta in [6, 63].
+__device__ __forceinline__ int quad_level(int pref)
+{
+    if (pref >= 64) return kLevels;
+    int l = (pref - 6) >> 1;
+    return l < kLevels ? l : kLevels;
+}
+
+}  // namespace hts
+#endif

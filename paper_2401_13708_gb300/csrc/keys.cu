@@ -1,0 +1,137 @@
+// keys.cu -- per-point preparation and polar keys (Sec. 4.1).
+//
+// prep_points: conformal factor il = 1 / (1 - |y|^2) (lambda / 2, Eq.
+//   PoincareMetric), the 32-byte point records, and the radial split
+//   coordinate (disk radius for Eq. EqualEmbeddingLengthsSplitting, cosh of
+//   the hyperbolic radius, (1 + |y|^2) / (1 - |y|^2), for Eq.
+//   EqualAreaSplitting) with the root annulus bounds reduced by atomic
+//   min / max on the bit patterns (exact for non-negative doubles).
+// make_keys: normalised coordinates rho^ = (c - c_min) / (c_max - c_min),
+//   phi^ = atan2 / 2 pi in [0, 1], each quantised to 29 bits and
+//   interleaved (digit l = 2 * radial bit + angular bit of level l, most
+//   significant first), so that the depth-l cell of the equal-length tree is
+//   the top 2l key bits.  The float64 steps use explicitly rounded
+//   intrinsics so no fused multiply-add changes a quantised bit.
+#include "hts_internal.cuh"
+
+namespace hts {
+namespace {
+
+constexpr int kBlock = 256;
+
+__global__ void init_minmax_kernel(unsigned long long *mm)
+{
+    mm[0] = 0x7FF0000000000000ull;  // +inf
+    mm[1] = 0ull;                   // +0
+}
+
+__global__ void prep_points_kernel(int n, const double2 *__restrict__ y, int split_rule, PointF *pts32,
+                                   PointD *pts64, double *radial, unsigned long long *mm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double c = 0.0;
+    bool ok = i < n;
+    if (ok) {
+        double2 p = y[i];
+        double n2 = __dadd_rn(__dmul_rn(p.x, p.x), __dmul_rn(p.y, p.y));
+        double il = __ddiv_rn(1.0, __dsub_rn(1.0, n2));
+        if (pts32) {
+            PointF r;
+            r.xh = (float)p.x;
+            r.yh = (float)p.y;
+            r.xl = (float)(p.x - (double)r.xh);
+            r.yl = (float)(p.y - (double)r.yh);
+            r.il = (float)il;
+            r.pad0 = r.pad1 = r.pad2 = 0.f;
+            pts32[i] = r;
+        }
+        if (pts64) pts64[i] = PointD{p.x, p.y, il, 0.0};
+        c = split_rule == HTS_EQUAL_AREA ? __ddiv_rn(__dadd_rn(1.0, n2), __dsub_rn(1.0, n2)) : __dsqrt_rn(n2);
+        radial[i] = c;
+    }
+    // block min / max, then one atomic each
+    __shared__ unsigned long long smin[kBlock / 32], smax[kBlock / 32];
+    unsigned long long b = (unsigned long long)__double_as_longlong(c);
+    unsigned long long vmin = ok ? b : 0x7FF0000000000000ull;
+    unsigned long long vmax = ok ? b : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long a = __shfl_xor_sync(0xffffffffu, vmin, o);
+        unsigned long long z = __shfl_xor_sync(0xffffffffu, vmax, o);
+        vmin = a < vmin ? a : vmin;
+        vmax = z > vmax ? z : vmax;
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        smin[w] = vmin;
+        smax[w] = vmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kBlock / 32; ++k) {
+            vmin = smin[k] < vmin ? smin[k] : vmin;
+            vmax = smax[k] > vmax ? smax[k] : vmax;
+        }
+        atomicMin(&mm[0], vmin);
+        atomicMax(&mm[1], vmax);
+    }
+}
+
+// Spread the low 29 bits of v to the odd/even positions of a 58-bit word.
+__device__ __forceinline__ uint64_t spread_bits(uint64_t v)
+{
+    v &= 0x1FFFFFFFull;
+    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t quantise(double u)
+{
+    double s = floor(__dmul_rn(u, (double)(1u << kLevels)));
+    uint64_t q = (uint64_t)s;
+    const uint64_t top = (1ull << kLevels) - 1;
+    return q > top ? top : q;
+}
+
+__global__ void make_keys_kernel(int n, const double2 *__restrict__ y, const double *__restrict__ radial,
+                                 const unsigned long long *__restrict__ mm, uint64_t *keys, uint32_t *idx)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo = __longlong_as_double((long long)mm[0]);
+    double hi = __longlong_as_double((long long)mm[1]);
+    double c = radial[i];
+    double rh = hi > lo ? __ddiv_rn(__dsub_rn(c, lo), __dsub_rn(hi, lo)) : 0.0;
+    double2 p = y[i];
+    double phi = atan2(p.y, p.x);
+    if (phi < 0.0) phi = __dadd_rn(phi, kTwoPi);
+    double ph = __ddiv_rn(phi, kTwoPi);
+    uint64_t qa = quantise(rh), qb = quantise(ph);
+    keys[i] = (spread_bits(qa) << 1) | spread_bits(qb);
+    idx[i] = (uint32_t)i;
+}
+
+}  // namespace
+
+void launch_prep_points(hts_ctx *c)
+{
+    int n = (int)c->n;
+    init_minmax_kernel<<<1, 1, 0, c->stream>>>(c->minmax);
+    bool f32 = c->cfg.precision == HTS_FP32_MIXED;
+    prep_points_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(
+        n, c->y, c->cfg.split_rule, f32 ? c->pts32 : nullptr, f32 ? nullptr : c->pts64, c->radial, c->minmax);
+    c->launches += 2;
+}
+
+void launch_make_keys(hts_ctx *c)
+{
+    int n = (int)c->n;
+    make_keys_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(n, c->y, c->radial, c->minmax, c->keys,
+                                                                         c->idx);
+    c->launches += 1;
+}
+
+}  // namespace hts

@@ -1,0 +1,378 @@
+// traverse.cu -- Barnes-Hut repulsion (Sec. 4.2, Eq. CellApproximation) and
+// the exact O(n^2) repulsion (Eq. KlGradientHyperbolicSplit, second sum).
+//
+// Warp-cooperative tree walk.  A warp takes 32 consecutive points in key
+// order (neighbouring cells, so the lanes' walks overlap) and visits the
+// pre-order node array with one warp-uniform cursor:
+//   - at an internal cell every active lane tests its own criterion
+//     r_cell / d(y_i, y_cell) < theta, written as delta_i,cell > thr_cell
+//     with thr = cosh(r_cell / theta) - 1 (cosh is increasing, so the test is
+//     exact and needs no transcendental);  a lane that accepts adds the cell
+//     term N_cell w^2 d dd/dy_i and becomes inactive until the cursor leaves
+//     the cell's subtree (pre-order index >= skip);
+//   - the warp descends (cursor + 1) if any active lane rejected the cell,
+//     otherwise it jumps to skip;
+//   - leaves add the exact pair term for every active lane, except the lane
+//     whose own point it is; depth-29 buckets add each of their points.
+// Each lane therefore accumulates exactly the terms of its own depth-first
+// walk; the warp visits the union of the 32 walks.  Node loads are
+// warp-uniform (one sector, broadcast) and stay in L1/L2.
+//
+// Per lane the pair term is reduced to a scalar times (Delta, s) and a w
+// for Z (see pair_terms_* in hts_internal.cuh); the result per point is
+//   F_rep,i = 4 il_i (R_Delta + il_i R_s y_i),   Z_i = sum N w,
+// written to the point's original index.
+#include <limits.h>
+
+#include "hts_internal.cuh"
+
+namespace hts {
+namespace {
+
+constexpr int kWalkBlock = 256;
+constexpr int kExactBlock = 256;
+
+__device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int k)
+{
+    const float4 *p = reinterpret_cast<const float4 *>(nodes + k);
+    float4 a = __ldg(p), b = __ldg(p + 1);
+    NodeF r;
+    r.xh = a.x;
+    r.yh = a.y;
+    r.xl = a.z;
+    r.yl = a.w;
+    r.il = b.x;
+    r.thr = b.y;
+    r.count = __float_as_int(b.z);
+    r.skip = __float_as_int(b.w);
+    return r;
+}
+
+template <int GF, bool COUNT>
+__global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF *__restrict__ nodes,
+                                                              const int *__restrict__ n_nodes,
+                                                              const PointF *__restrict__ spts,
+                                                              const uint32_t *__restrict__ idx, double2 *frep,
+                                                              double *zi, unsigned long long *counters,
+                                                              int *status)
+{
+    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp * 32 >= n) return;
+    const int p = warp * 32 + lane;
+    const bool valid = p < n;
+    const PointF q = spts[valid ? p : n - 1];
+    const float twoil = 2.0f * q.il;
+    float rx = 0.f, ry = 0.f, rs = 0.f, z = 0.f;
+    const int m = min(*n_nodes, 2 * n);
+    int resume = valid ? 0 : INT_MAX;
+    int node = 0;
+    unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
+    while (node < m) {
+        const NodeF c = load_node(nodes, node);
+        const bool active = node >= resume;
+        int next = node + 1;
+        if (c.count >= 2) {
+            float dx = (q.xh - c.xh) + (q.xl - c.xl);
+            float dy = (q.yh - c.yh) + (q.yl - c.yl);
+            float s = fmaf(dx, dx, dy * dy);
+            float delta = s * twoil * c.il;
+            bool acc = active && delta > c.thr;
+            if (acc) {
+                PairF t = pair_terms_f32<GF>(delta);
+                float mult = (float)c.count;
+                float k = mult * t.rep * c.il;
+                rx = fmaf(k, dx, rx);
+                ry = fmaf(k, dy, ry);
+                rs = fmaf(k, s, rs);
+                z = fmaf(mult, t.w, z);
+                resume = c.skip;
+                if (COUNT) ++c_acc;
+            }
+            if (!__any_sync(0xffffffffu, active && !acc)) next = c.skip;
+        } else if (c.count == 1) {
+            if (active && __float_as_int(c.thr) != p) {
+                float dx = (q.xh - c.xh) + (q.xl - c.xl);
+                float dy = (q.yh - c.yh) + (q.yl - c.yl);
+                float s = fmaf(dx, dx, dy * dy);
+                PairF t = pair_terms_f32<GF>(s * twoil * c.il);
+                float k = t.rep * c.il;
+                rx = fmaf(k, dx, rx);
+                ry = fmaf(k, dy, ry);
+                rs = fmaf(k, s, rs);
+                z += t.w;
+                if (COUNT) ++c_pair;
+            }
+        } else {
+            const int lo = __float_as_int(c.thr), cnt = -c.count;
+            if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
+                for (int k2 = 0; k2 < cnt; ++k2) {
+                    if (lo + k2 == p) continue;
+                    PointF o = spts[lo + k2];
+                    float dx = (q.xh - o.xh) + (q.xl - o.xl);
+                    float dy = (q.yh - o.yh) + (q.yl - o.yl);
+                    float s = fmaf(dx, dx, dy * dy);
+                    PairF t = pair_terms_f32<GF>(s * twoil * o.il);
+                    float k = t.rep * o.il;
+                    rx = fmaf(k, dx, rx);
+                    ry = fmaf(k, dy, ry);
+                    rs = fmaf(k, s, rs);
+                    z += t.w;
+                    if (COUNT) ++c_pair;
+                }
+            }
+        }
+        if (COUNT && lane == 0) ++c_visit;
+        if (next <= node) {  // a skip index that does not advance: corrupt tree
+            if (lane == 0) atomicOr(status, 4);
+            break;
+        }
+        node = next;
+    }
+    if (valid) {
+        const uint32_t i = idx[p];
+        double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
+        double il = (double)q.il;
+        double rsd = il * (double)rs;
+        frep[i] = make_double2(4.0 * il * ((double)rx + rsd * x), 4.0 * il * ((double)ry + rsd * y));
+        zi[i] = (double)z;
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) {
+            c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o);
+            c_pair += __shfl_xor_sync(0xffffffffu, c_pair, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&counters[0], c_acc);
+            atomicAdd(&counters[1], c_pair);
+            atomicAdd(&counters[2], c_visit);
+            atomicAdd(&counters[3], (unsigned long long)min(32, n - warp * 32));
+        }
+    }
+}
+
+template <int GF, bool COUNT>
+__global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD *__restrict__ nodes,
+                                                              const int *__restrict__ n_nodes,
+                                                              const PointD *__restrict__ spts,
+                                                              const uint32_t *__restrict__ idx, double2 *frep,
+                                                              double *zi, unsigned long long *counters,
+                                                              int *status)
+{
+    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp * 32 >= n) return;
+    const int p = warp * 32 + lane;
+    const bool valid = p < n;
+    const PointD q = spts[valid ? p : n - 1];
+    const double twoil = 2.0 * q.il;
+    double rx = 0, ry = 0, rs = 0, z = 0;
+    const int m = min(*n_nodes, 2 * n);
+    int resume = valid ? 0 : INT_MAX;
+    int node = 0;
+    unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
+    while (node < m) {
+        const NodeD c = nodes[node];
+        const bool active = node >= resume;
+        int next = node + 1;
+        if (c.count >= 2) {
+            double dx = q.x - c.x, dy = q.y - c.y;
+            double s = fma(dx, dx, dy * dy);
+            double delta = s * twoil * c.il;
+            bool acc = active && delta > c.thr;
+            if (acc) {
+                PairD t = pair_terms_f64<GF>(delta);
+                double mult = (double)c.count;
+                double k = mult * t.rep * c.il;
+                rx = fma(k, dx, rx);
+                ry = fma(k, dy, ry);
+                rs = fma(k, s, rs);
+                z = fma(mult, t.w, z);
+                resume = c.skip;
+                if (COUNT) ++c_acc;
+            }
+            if (!__any_sync(0xffffffffu, active && !acc)) next = c.skip;
+        } else if (c.count == 1) {
+            if (active && c.pos != p) {
+                double dx = q.x - c.x, dy = q.y - c.y;
+                double s = fma(dx, dx, dy * dy);
+                PairD t = pair_terms_f64<GF>(s * twoil * c.il);
+                double k = t.rep * c.il;
+                rx = fma(k, dx, rx);
+                ry = fma(k, dy, ry);
+                rs = fma(k, s, rs);
+                z += t.w;
+                if (COUNT) ++c_pair;
+            }
+        } else {
+            const int lo = c.pos, cnt = -c.count;
+            if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
+                for (int k2 = 0; k2 < cnt; ++k2) {
+                    if (lo + k2 == p) continue;
+                    PointD o = spts[lo + k2];
+                    double dx = q.x - o.x, dy = q.y - o.y;
+                    double s = fma(dx, dx, dy * dy);
+                    PairD t = pair_terms_f64<GF>(s * twoil * o.il);
+                    double k = t.rep * o.il;
+                    rx = fma(k, dx, rx);
+                    ry = fma(k, dy, ry);
+                    rs = fma(k, s, rs);
+                    z += t.w;
+                    if (COUNT) ++c_pair;
+                }
+            }
+        }
+        if (COUNT && lane == 0) ++c_visit;
+        if (next <= node) {
+            if (lane == 0) atomicOr(status, 4);
+            break;
+        }
+        node = next;
+    }
+    if (valid) {
+        const uint32_t i = idx[p];
+        double rsd = q.il * rs;
+        frep[i] = make_double2(4.0 * q.il * (rx + rsd * q.x), 4.0 * q.il * (ry + rsd * q.y));
+        zi[i] = z;
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) {
+            c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o);
+            c_pair += __shfl_xor_sync(0xffffffffu, c_pair, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&counters[0], c_acc);
+            atomicAdd(&counters[1], c_pair);
+            atomicAdd(&counters[2], c_visit);
+            atomicAdd(&counters[3], (unsigned long long)min(32, n - warp * 32));
+        }
+    }
+}
+
+// Exact repulsion: one thread per point i, tiles of 256 points j staged in
+// shared memory, every pair j != i.
+template <int GF>
+__global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(int n, const PointF *__restrict__ pts, double2 *frep,
+                                                                double *zi)
+{
+    __shared__ PointF tile[kExactBlock];
+    const int i = blockIdx.x * kExactBlock + threadIdx.x;
+    const PointF q = pts[i < n ? i : n - 1];
+    const float twoil = 2.0f * q.il;
+    float rx = 0.f, ry = 0.f, rs = 0.f, z = 0.f;
+    for (int base = 0; base < n; base += kExactBlock) {
+        int j = base + threadIdx.x;
+        if (j < n) tile[threadIdx.x] = pts[j];
+        __syncthreads();
+        const int cnt = min(kExactBlock, n - base);
+        for (int k = 0; k < cnt; ++k) {
+            if (base + k == i) continue;
+            const PointF o = tile[k];
+            float dx = (q.xh - o.xh) + (q.xl - o.xl);
+            float dy = (q.yh - o.yh) + (q.yl - o.yl);
+            float s = fmaf(dx, dx, dy * dy);
+            PairF t = pair_terms_f32<GF>(s * twoil * o.il);
+            float kk = t.rep * o.il;
+            rx = fmaf(kk, dx, rx);
+            ry = fmaf(kk, dy, ry);
+            rs = fmaf(kk, s, rs);
+            z += t.w;
+        }
+        __syncthreads();
+    }
+    if (i < n) {
+        double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
+        double il = (double)q.il;
+        double rsd = il * (double)rs;
+        frep[i] = make_double2(4.0 * il * ((double)rx + rsd * x), 4.0 * il * ((double)ry + rsd * y));
+        zi[i] = (double)z;
+    }
+}
+
+template <int GF>
+__global__ void __launch_bounds__(kExactBlock) exact_f64_kernel(int n, const PointD *__restrict__ pts, double2 *frep,
+                                                                double *zi)
+{
+    __shared__ PointD tile[kExactBlock];
+    const int i = blockIdx.x * kExactBlock + threadIdx.x;
+    const PointD q = pts[i < n ? i : n - 1];
+    const double twoil = 2.0 * q.il;
+    double rx = 0, ry = 0, rs = 0, z = 0;
+    for (int base = 0; base < n; base += kExactBlock) {
+        int j = base + threadIdx.x;
+        if (j < n) tile[threadIdx.x] = pts[j];
+        __syncthreads();
+        const int cnt = min(kExactBlock, n - base);
+        for (int k = 0; k < cnt; ++k) {
+            if (base + k == i) continue;
+            const PointD o = tile[k];
+            double dx = q.x - o.x, dy = q.y - o.y;
+            double s = fma(dx, dx, dy * dy);
+            PairD t = pair_terms_f64<GF>(s * twoil * o.il);
+            double kk = t.rep * o.il;
+            rx = fma(kk, dx, rx);
+            ry = fma(kk, dy, ry);
+            rs = fma(kk, s, rs);
+            z += t.w;
+        }
+        __syncthreads();
+    }
+    if (i < n) {
+        double rsd = q.il * rs;
+        frep[i] = make_double2(4.0 * q.il * (rx + rsd * q.x), 4.0 * q.il * (ry + rsd * q.y));
+        zi[i] = z;
+    }
+}
+
+}  // namespace
+
+void launch_walk(hts_ctx *c)
+{
+    const int n = (int)c->n;
+    const int warps = (n + 31) / 32;
+    const int blocks = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
+    const bool cnt = c->counters_on != 0;
+    if (cnt) cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream);
+    c->launches += 1;
+    if (c->cfg.precision == HTS_FP32_MIXED) {
+#define HTS_WALK(GF, CT) \
+    walk_f32_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes32, c->n_nodes, c->spts32, c->idx, \
+                                                                  c->frep, c->zi, c->counters, c->status)
+        if (c->cfg.grad_form == HTS_EXACT_KL) {
+            if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
+        } else {
+            if (cnt) HTS_WALK(1, true); else HTS_WALK(1, false);
+        }
+#undef HTS_WALK
+    } else {
+#define HTS_WALK(GF, CT) \
+    walk_f64_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes64, c->n_nodes, c->spts64, c->idx, \
+                                                                  c->frep, c->zi, c->counters, c->status)
+        if (c->cfg.grad_form == HTS_EXACT_KL) {
+            if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
+        } else {
+            if (cnt) HTS_WALK(1, true); else HTS_WALK(1, false);
+        }
+#undef HTS_WALK
+    }
+}
+
+void launch_exact(hts_ctx *c)
+{
+    const int n = (int)c->n;
+    const int blocks = (n + kExactBlock - 1) / kExactBlock;
+    c->launches += 1;
+    if (c->cfg.precision == HTS_FP32_MIXED) {
+        if (c->cfg.grad_form == HTS_EXACT_KL)
+            exact_f32_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi);
+        else
+            exact_f32_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi);
+    } else {
+        if (c->cfg.grad_form == HTS_EXACT_KL)
+            exact_f64_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi);
+        else
+            exact_f64_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi);
+    }
+}
+
+}  // namespace hts

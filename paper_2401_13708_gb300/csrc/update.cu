@@ -1,0 +1,147 @@
+// update.cu -- Z, the gradient and the Riemannian step, all in float64.
+//
+// reduce_z   Z = sum_i Z_i in a fixed order (one block, strided partial sums
+//            then a shared-memory tree), so the value is reproducible.
+// update     g_i = 4 (exag F_attr,i - F_rep,i / Z)  (Eq. KlGradientHyperbolicSplit
+//            with the exaggeration of Sec. 5.1), then
+//              r_i = lambda_i^-metric_pow g_i  ("product of lambda^-1 with the
+//                    variation", Sec. 4.2; lambda = 2 / (1 - |y|^2), Eq. PoincareMetric)
+//              optional gains (+0.2 on sign disagreement of g and v, *0.8
+//                    otherwise, floor 0.01),
+//              v_i <- momentum v_i - lr gains r_i,
+//              y_i <- proj(exp_{y_i}(v_i)),  exp_y(v) = y (+) tanh(lambda |v| / 2) v / |v|
+//                    with Moebius addition (+) (Sec. 4.2), proj of Eq.
+//                    HyperbolicProjection: radius 1 - eps once |y| >= 1 - eps/2.
+//            A non-finite result sets bit 1 of the status word.
+#include "hts_internal.cuh"
+
+namespace hts {
+namespace {
+
+constexpr int kBlock = 256;
+
+__global__ void reduce_sum_kernel(int n, const double *__restrict__ v, double *out)
+{
+    __shared__ double sh[1024];
+    double a = 0;
+    for (int k = threadIdx.x; k < n; k += 1024) a += v[k];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+struct UpdateArgs {
+    int n;
+    double2 *y, *vel, *gains;
+    const double2 *fattr, *frep;
+    const double *Z;
+    double exag, lr, mom, eps;
+    int metric_pow, use_gains, do_step;
+    double2 *g_out;
+    int *status;
+};
+
+__global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= A.n) return;
+    const double Z = *A.Z;
+    const double invZ = Z > 0.0 ? 1.0 / Z : 0.0;
+    const double2 fa = A.fattr[i], fr = A.frep[i];
+    const double gx = 4.0 * (A.exag * fa.x - fr.x * invZ);
+    const double gy = 4.0 * (A.exag * fa.y - fr.y * invZ);
+    if (A.g_out) A.g_out[i] = make_double2(gx, gy);
+    if (!A.do_step) return;
+    double2 p = A.y[i];
+    double2 v = A.vel[i];
+    const double n2 = p.x * p.x + p.y * p.y;
+    const double lam = 2.0 / (1.0 - n2);
+    const double sc = A.metric_pow == 2 ? 1.0 / (lam * lam) : 1.0 / lam;
+    double kx = 1.0, ky = 1.0;
+    if (A.use_gains) {
+        double2 gn = A.gains[i];
+        gn.x = ((gx > 0.0) == (v.x > 0.0)) ? gn.x * 0.8 : gn.x + 0.2;
+        gn.y = ((gy > 0.0) == (v.y > 0.0)) ? gn.y * 0.8 : gn.y + 0.2;
+        gn.x = fmax(gn.x, 0.01);
+        gn.y = fmax(gn.y, 0.01);
+        A.gains[i] = gn;
+        kx = gn.x;
+        ky = gn.y;
+    }
+    v.x = A.mom * v.x - A.lr * kx * (gx * sc);
+    v.y = A.mom * v.y - A.lr * ky * (gy * sc);
+    const double nv = sqrt(v.x * v.x + v.y * v.y);
+    double2 q = p;
+    if (nv > 0.0) {
+        const double t = tanh(lam * nv / 2.0);
+        const double ux = t * v.x / nv, uy = t * v.y / nv;
+        const double pu = p.x * ux + p.y * uy;
+        const double nu = ux * ux + uy * uy;
+        const double ca = 1.0 + 2.0 * pu + nu;
+        const double cb = 1.0 - n2;
+        const double den = 1.0 + 2.0 * pu + n2 * nu;
+        q.x = (ca * p.x + cb * ux) / den;
+        q.y = (ca * p.y + cb * uy) / den;
+    }
+    const double r = sqrt(q.x * q.x + q.y * q.y);
+    if (r >= 1.0 - A.eps / 2.0) {
+        const double f = (1.0 - A.eps) / r;
+        q.x *= f;
+        q.y *= f;
+    }
+    if (!isfinite(q.x) || !isfinite(q.y) || !isfinite(v.x) || !isfinite(v.y)) atomicOr(A.status, 1);
+    A.y[i] = q;
+    A.vel[i] = v;
+}
+
+// status bit 64: a point outside the open disk or non-finite
+__global__ void check_y_kernel(int n, const double2 *__restrict__ y, int *status)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    double2 p = y[i];
+    double n2 = p.x * p.x + p.y * p.y;
+    if (!isfinite(p.x) || !isfinite(p.y) || !(n2 < 1.0)) atomicOr(status, 64);
+}
+
+}  // namespace
+
+void launch_reduce_z(hts_ctx *c)
+{
+    reduce_sum_kernel<<<1, 1024, 0, c->stream>>>((int)c->n, c->zi, c->dscal);
+    c->launches += 1;
+}
+
+void launch_update(hts_ctx *c, double exag, double lr, double mom, double2 *g_out, int do_step)
+{
+    UpdateArgs A;
+    A.n = (int)c->n;
+    A.y = c->y;
+    A.vel = c->vel;
+    A.gains = c->gains;
+    A.fattr = c->fattr;
+    A.frep = c->frep;
+    A.Z = c->dscal;
+    A.exag = exag;
+    A.lr = lr;
+    A.mom = mom;
+    A.eps = c->cfg.eps;
+    A.metric_pow = c->cfg.metric_pow;
+    A.use_gains = c->cfg.use_gains;
+    A.do_step = do_step;
+    A.g_out = g_out;
+    A.status = c->status;
+    update_kernel<<<(A.n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(A);
+    c->launches += 1;
+}
+
+void launch_check_y(hts_ctx *c)
+{
+    check_y_kernel<<<((int)c->n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>((int)c->n, c->y, c->status);
+}
+
+}  // namespace hts
