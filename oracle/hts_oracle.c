@@ -195,20 +195,32 @@ void ho_einstein_midpoint(int64_t n, const double *y, double *out)
     klein_to_poincare((double)sg, (double)sx, (double)sy, out);
 }
 
-/* Longest internal distance of the polar quad [r0, r1] x [phi, phi + dphi]
- * (Sec. 4.1, reading R3): the max of the diagonal, the radial edge and the
- * outer-arc chord, each a hyperbolic distance. */
-double ho_rcell(double r0, double r1, double dphi)
+/* Hyperbolic distance between the polar points (ra, 0) and (rb, dphi),
+ * given their exact radial gap drr = rb - ra.  The law of cosines written
+ * as |p - q|^2 = drr^2 + 4 ra rb sin^2(dphi / 2) and 1 - r^2 = (1 - r)(1 + r)
+ * avoid the cancellation of the Cartesian form for small cells. */
+static double polar_dist(double ra, double rb, double drr, double dphi)
 {
-    double p0[2] = {r0, 0.0};
-    double p1[2] = {r1 * cos(dphi), r1 * sin(dphi)};
-    double q0[2] = {r1, 0.0};
-    double diag = ho_dist(p0, p1);
-    double radial = ho_dist(p0, q0);
-    double arc = ho_dist(q0, p1);
+    double sh = sin(dphi / 2.0);
+    double s = drr * drr + 4.0 * ra * rb * sh * sh;
+    double delta = 2.0 * s / (((1.0 - ra) * (1.0 + ra)) * ((1.0 - rb) * (1.0 + rb)));
+    return ho_acosh1p(delta);
+}
+
+/* Longest internal distance of the polar quad [r0, r1] x [phi, phi + dphi]
+ * with radial gap dr = r1 - r0 (Sec. 4.1, reading R3): the max of the
+ * diagonal, the radial edge and the outer-arc chord, each a hyperbolic
+ * distance. */
+static double rcell_gap(double r0, double r1, double dr, double dphi)
+{
+    double diag = polar_dist(r0, r1, dr, dphi);
+    double radial = polar_dist(r0, r1, dr, 0.0);
+    double arc = polar_dist(r1, r1, 0.0, dphi);
     double m = diag > radial ? diag : radial;
     return m > arc ? m : arc;
 }
+
+double ho_rcell(double r0, double r1, double dphi) { return rcell_gap(r0, r1, r1 - r0, dphi); }
 
 /* ------------------------------------------------------------------------ */
 /* Pair terms shared by the exact and Barnes-Hut sums                        */
@@ -362,6 +374,22 @@ static double radius_of(double c, int split_rule)
     return c;
 }
 
+/* Size of the depth-`depth` cell with radial index ia: disk radii r0, r1 of
+ * its bounds and their gap.  The gap in the split coordinate is
+ * span * 2^-depth exactly; under equal-area splitting the radius gap follows
+ * from r^2 = 1 - 2 / (c + 1):  r1 - r0 = 2 dc / ((c0 + 1)(c1 + 1)(r0 + r1)). */
+static double cell_rcell(double lo, double hi, int64_t ia, int depth, int split_rule)
+{
+    double scale = ldexp(1.0, -depth);
+    double span = hi - lo;
+    double c0 = lo + span * ((double)ia * scale);
+    double c1 = lo + span * ((double)(ia + 1) * scale);
+    double dc = span * scale;
+    double r0 = radius_of(c0, split_rule), r1 = radius_of(c1, split_rule);
+    double dr = split_rule == 1 ? (r0 + r1 > 0.0 ? 2.0 * dc / ((c0 + 1.0) * (c1 + 1.0) * (r0 + r1)) : 0.0) : dc;
+    return rcell_gap(r0, r1, dr, HO_TWO_PI * scale);
+}
+
 /* Normalised coordinates (R4, R5). */
 static void normalise(int64_t n, const double *y, int split_rule, double *uh, double *vh, double *lo, double *hi)
 {
@@ -500,15 +528,10 @@ static void finish_nodes(otree *t, const double *y)
         } else {
             klein_to_poincare((double)nd->sg, (double)nd->sux, (double)nd->suy, nd->ycell);
         }
-        if (nd->depth == 0) {
+        if (nd->depth == 0)
             nd->rcell = INFINITY;
-        } else {
-            double scale = ldexp(1.0, -nd->depth);
-            double span = t->radial_hi - t->radial_lo;
-            double c0 = t->radial_lo + span * (nd->ia * scale);
-            double c1 = t->radial_lo + span * ((nd->ia + 1) * scale);
-            nd->rcell = ho_rcell(radius_of(c0, t->split_rule), radius_of(c1, t->split_rule), HO_TWO_PI * scale);
-        }
+        else
+            nd->rcell = cell_rcell(t->radial_lo, t->radial_hi, nd->ia, nd->depth, t->split_rule);
     }
 }
 
@@ -642,11 +665,7 @@ static void export_key_rec(const keytree_t *kt, int depth, int64_t lo, int64_t h
         uint64_t prefix = key0 >> (2 * (HO_LEVELS - depth));
         uint64_t ia = 0;
         for (int b = 0; b < depth; ++b) ia |= ((prefix >> (2 * b + 1)) & 1u) << b;
-        double scale = ldexp(1.0, -depth);
-        double span = kt->radial_hi - kt->radial_lo;
-        double c0 = kt->radial_lo + span * ((double)ia * scale);
-        double c1 = kt->radial_lo + span * ((double)(ia + 1) * scale);
-        rc = ho_rcell(radius_of(c0, kt->split_rule), radius_of(c1, kt->split_rule), HO_TWO_PI * scale);
+        rc = cell_rcell(kt->radial_lo, kt->radial_hi, (int64_t)ia, depth, kt->split_rule);
     }
     uint64_t prefix = depth ? key0 >> (2 * (HO_LEVELS - depth)) : 0;
     emit(ex, depth, prefix, hi - lo, depth == HO_LEVELS ? mfirst : -1, yc, rc);

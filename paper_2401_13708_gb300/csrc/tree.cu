@@ -156,13 +156,13 @@ __global__ void quad_mark_kernel(int n, const int *__restrict__ parent, const in
     }
 }
 
-__device__ __forceinline__ double hyp_dist(double ax, double ay, double bx, double by)
+// Hyperbolic distance between the polar points (ra, 0) and (rb, dphi) with
+// exact radial gap drr = rb - ra: |p - q|^2 = drr^2 + 4 ra rb sin^2(dphi/2),
+// 1 - r^2 = (1 - r)(1 + r) -- no cancellation for small cells.
+__device__ __forceinline__ double polar_dist(double ra, double rb, double drr, double sh)
 {
-    double dx = ax - bx, dy = ay - by;
-    double s = dx * dx + dy * dy;
-    double al = 1.0 - (ax * ax + ay * ay);
-    double be = 1.0 - (bx * bx + by * by);
-    double delta = 2.0 * s / (al * be);
+    double s = drr * drr + 4.0 * ra * rb * sh * sh;
+    double delta = 2.0 * s / (((1.0 - ra) * (1.0 + ra)) * ((1.0 - rb) * (1.0 + rb)));
     return log1p(delta + sqrt(delta * (delta + 2.0)));
 }
 
@@ -171,20 +171,24 @@ __device__ __forceinline__ double radius_of(double c, int rule)
     return rule == HTS_EQUAL_AREA ? sqrt((c - 1.0) / (c + 1.0)) : c;
 }
 
-// Longest internal distance of the depth-`ell` polar quad with radial index a.
+// Longest internal distance of the depth-`ell` polar quad with radial index a:
+// max of diagonal, radial edge and outer-arc chord (Sec. 4.1).  The gap in the
+// split coordinate is span * 2^-ell exactly; for equal-area splitting
+// r1 - r0 = 2 dc / ((c0 + 1)(c1 + 1)(r0 + r1)) since r^2 = 1 - 2 / (c + 1).
 __device__ double cell_size(double lo, double hi, uint64_t a, int ell, int rule)
 {
     double scale = ldexp(1.0, -ell);
     double span = hi - lo;
     double c0 = lo + span * ((double)a * scale);
     double c1 = lo + span * ((double)(a + 1) * scale);
+    double dc = span * scale;
     double r0 = radius_of(c0, rule), r1 = radius_of(c1, rule);
-    double dphi = kTwoPi * scale;
-    double sn, cs;
-    sincos(dphi, &sn, &cs);
-    double diag = hyp_dist(r0, 0.0, r1 * cs, r1 * sn);
-    double radial = hyp_dist(r0, 0.0, r1, 0.0);
-    double arc = hyp_dist(r1, 0.0, r1 * cs, r1 * sn);
+    double dr = rule == HTS_EQUAL_AREA ? (r0 + r1 > 0.0 ? 2.0 * dc / ((c0 + 1.0) * (c1 + 1.0) * (r0 + r1)) : 0.0)
+                                       : dc;
+    double sh = sin(kTwoPi * scale / 2.0);
+    double diag = polar_dist(r0, r1, dr, sh);
+    double radial = polar_dist(r0, r1, dr, 0.0);
+    double arc = polar_dist(r1, r1, 0.0, sh);
     return fmax(fmax(diag, radial), arc);
 }
 
