@@ -110,8 +110,11 @@ static double pd_delta(const double *a, const double *b)
 double ho_dist(const double *a, const double *b) { return ho_acosh1p(pd_delta(a, b)); }
 
 /* Derivative of d^H(y_i, y_j) with respect to y_i, Eq. PoincareDistanceDerivative:
- *   4 ((|y_j|^2 - 2<y_i,y_j> + 1) y_i / alpha - y_j) / (alpha beta sqrt(gamma^2 - 1)),
- * with sqrt(gamma^2 - 1) evaluated as sqrt(delta (delta + 2)).  Undefined at
+ *   4 ((|y_j|^2 - 2<y_i,y_j> + 1) y_i / alpha - y_j) / (alpha beta sqrt(gamma^2 - 1)).
+ * Since |y_j|^2 - 2<y_i,y_j> + 1 = |y_i - y_j|^2 + alpha = s + alpha, the
+ * numerator vector equals (y_i - y_j) + (s / alpha) y_i; that form is used
+ * because the printed one cancels for close pairs near the rim.
+ * sqrt(gamma^2 - 1) is evaluated as sqrt(delta (delta + 2)).  Undefined at
  * y_i == y_j; returns 0 there (callers only use d * dd/dy, which tends to 0). */
 void ho_dist_grad(const double *yi, const double *yj, double *out)
 {
@@ -122,10 +125,9 @@ void ho_dist_grad(const double *yi, const double *yj, double *out)
     if (s == 0.0) { out[0] = 0.0; out[1] = 0.0; return; }
     double delta = 2.0 * s / (al * be);
     double root = sqrt(delta * (delta + 2.0));
-    double c = sq2(yj[0], yj[1]) - 2.0 * (yi[0] * yj[0] + yi[1] * yj[1]) + 1.0;
     double den = al * be * root;
-    out[0] = 4.0 * (c * yi[0] / al - yj[0]) / den;
-    out[1] = 4.0 * (c * yi[1] / al - yj[1]) / den;
+    out[0] = 4.0 * (dx + (s / al) * yi[0]) / den;
+    out[1] = 4.0 * (dy + (s / al) * yi[1]) / den;
 }
 
 /* Moebius addition a (+) b, Sec. 4.2. */

@@ -158,17 +158,20 @@ __global__ void quad_mark_kernel(int n, const int *__restrict__ parent, const in
 
 // Hyperbolic distance between the polar points (ra, 0) and (rb, dphi) with
 // exact radial gap drr = rb - ra: |p - q|^2 = drr^2 + 4 ra rb sin^2(dphi/2),
-// 1 - r^2 = (1 - r)(1 + r) -- no cancellation for small cells.
+// 1 - r^2 = (1 - r)(1 + r) -- no cancellation for small cells.  Explicitly
+// rounded operations keep the cell geometry free of fused multiply-adds.
 __device__ __forceinline__ double polar_dist(double ra, double rb, double drr, double sh)
 {
-    double s = drr * drr + 4.0 * ra * rb * sh * sh;
-    double delta = 2.0 * s / (((1.0 - ra) * (1.0 + ra)) * ((1.0 - rb) * (1.0 + rb)));
-    return log1p(delta + sqrt(delta * (delta + 2.0)));
+    double s = __dadd_rn(__dmul_rn(drr, drr), __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0, ra), rb), sh), sh));
+    double den = __dmul_rn(__dmul_rn(__dsub_rn(1.0, ra), __dadd_rn(1.0, ra)),
+                           __dmul_rn(__dsub_rn(1.0, rb), __dadd_rn(1.0, rb)));
+    double delta = __ddiv_rn(__dmul_rn(2.0, s), den);
+    return log1p(__dadd_rn(delta, __dsqrt_rn(__dmul_rn(delta, __dadd_rn(delta, 2.0)))));
 }
 
 __device__ __forceinline__ double radius_of(double c, int rule)
 {
-    return rule == HTS_EQUAL_AREA ? sqrt((c - 1.0) / (c + 1.0)) : c;
+    return rule == HTS_EQUAL_AREA ? __dsqrt_rn(__ddiv_rn(__dsub_rn(c, 1.0), __dadd_rn(c, 1.0))) : c;
 }
 
 // Longest internal distance of the depth-`ell` polar quad with radial index a:
@@ -178,14 +181,18 @@ __device__ __forceinline__ double radius_of(double c, int rule)
 __device__ double cell_size(double lo, double hi, uint64_t a, int ell, int rule)
 {
     double scale = ldexp(1.0, -ell);
-    double span = hi - lo;
-    double c0 = lo + span * ((double)a * scale);
-    double c1 = lo + span * ((double)(a + 1) * scale);
-    double dc = span * scale;
+    double span = __dsub_rn(hi, lo);
+    double c0 = __dadd_rn(lo, __dmul_rn(span, __dmul_rn((double)a, scale)));
+    double c1 = __dadd_rn(lo, __dmul_rn(span, __dmul_rn((double)(a + 1), scale)));
+    double dc = __dmul_rn(span, scale);
     double r0 = radius_of(c0, rule), r1 = radius_of(c1, rule);
-    double dr = rule == HTS_EQUAL_AREA ? (r0 + r1 > 0.0 ? 2.0 * dc / ((c0 + 1.0) * (c1 + 1.0) * (r0 + r1)) : 0.0)
-                                       : dc;
-    double sh = sin(kTwoPi * scale / 2.0);
+    double dr = dc;
+    if (rule == HTS_EQUAL_AREA) {
+        double rs = __dadd_rn(r0, r1);
+        dr = rs > 0.0 ? __ddiv_rn(__dmul_rn(2.0, dc), __dmul_rn(__dmul_rn(__dadd_rn(c0, 1.0), __dadd_rn(c1, 1.0)), rs))
+                      : 0.0;
+    }
+    double sh = sin(__dmul_rn(kTwoPi, scale) / 2.0);
     double diag = polar_dist(r0, r1, dr, sh);
     double radial = polar_dist(r0, r1, dr, 0.0);
     double arc = polar_dist(r1, r1, 0.0, sh);

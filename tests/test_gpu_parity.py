@@ -240,7 +240,10 @@ def test_degenerate_inputs(case, prec):
             assert Z == 0 and np.all(g == 0)
             continue
         assert Z == pytest.approx(ref["Z"], rel=tol)
-        assert rel(g, ref["g"]) < tol
+        # compare against the size of the two force terms: g itself can vanish
+        # (two points with p = q balance exactly)
+        scale = 4 * (np.linalg.norm(ref["fattr"]) + np.linalg.norm(ref["frep"]) / ref["Z"])
+        assert np.linalg.norm(g - ref["g"]) <= tol * scale
         t.step(3, theta, 1.0, 0.1, 0.5)
         yy = t.get_Y()
         assert np.all(np.linalg.norm(yy, axis=1) < 1)

@@ -82,6 +82,38 @@ def test_distance_gradient_finite_difference():
         assert np.allclose(g, fd, rtol=1e-6, atol=1e-8)
 
 
+def test_distance_gradient_accuracy_near_rim():
+    # Eq. PoincareDistanceDerivative evaluated literally with 60-digit decimal
+    # arithmetic on the same float64 inputs: the oracle must hold 1e-10
+    # relative accuracy for close pairs near the boundary of the disk.
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    rng = np.random.default_rng(12)
+    worst = 0.0
+    for _ in range(200):
+        r = 1 - 10 ** rng.uniform(-6, -1.5)
+        phi = rng.uniform(0, 2 * np.pi)
+        yi = np.array([r * math.cos(phi), r * math.sin(phi)])
+        off = 10 ** rng.uniform(-9, -2) * rng.normal(size=2)
+        yj = yi + off
+        if yj @ yj >= 1:
+            yj = yi - off
+        a = [Decimal(float(v)) for v in yi]
+        b = [Decimal(float(v)) for v in yj]
+        al = 1 - a[0] ** 2 - a[1] ** 2
+        be = 1 - b[0] ** 2 - b[1] ** 2
+        s = (a[0] - b[0]) ** 2 + (a[1] - b[1]) ** 2
+        gam = 1 + 2 * s / (al * be)
+        c = b[0] ** 2 + b[1] ** 2 - 2 * (a[0] * b[0] + a[1] * b[1]) + 1
+        den = al * be * (gam * gam - 1).sqrt()
+        ref = np.array([float(4 * (c * a[k] / al - b[k]) / den) for k in range(2)])
+        got = oracle.dist_grad(yi, yj)
+        worst = max(worst, np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        dref = float(((gam + (gam * gam - 1).sqrt())).ln())
+        assert oracle.dist(yi, yj) == pytest.approx(dref, rel=1e-10)
+    assert worst < 1e-10, worst
+
+
 def test_mobius_group_identities():
     rng = np.random.default_rng(3)
     y = rand_disk(rng, 20, 0.97)
