@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error gate / CPU baseline")
     ap.add_argument("--sample-rows", type=int, default=10000)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cache", default="", help="directory to keep the generated workload in (reused if present)")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="FP32-mixed steps only (for a profiler): no FP64 arm, e2e or oracle")
     return ap.parse_args()
 
 
@@ -145,7 +148,19 @@ class ClockSampler:
 def workload(args, device):
     from paper_2401_13708_gb300 import inputs
     t0 = time.time()
-    w = inputs.make_config(5, seed=args.seed, device=device, n=args.n)
+    path = None
+    if args.cache:
+        os.makedirs(args.cache, exist_ok=True)
+        path = os.path.join(args.cache, f"cfg5_n{args.n}_s{args.seed}.npz")
+    if path and os.path.exists(path):
+        z = np.load(path)
+        w = inputs.Workload(name=inputs.CONFIG_NAMES[5], n=int(z["indptr"].shape[0] - 1), indptr=z["indptr"],
+                            indices=z["indices"], values=z["values"], y0=z["y0"], labels=z["labels"],
+                            perplexity=30.0)
+    else:
+        w = inputs.make_config(5, seed=args.seed, device=device, n=args.n)
+        if path:
+            np.savez(path, indptr=w.indptr, indices=w.indices, values=w.values, y0=w.y0, labels=w.labels)
     y = inputs.spread_embedding(w.labels, args.seed)
     return w, y, time.time() - t0
 
@@ -170,25 +185,28 @@ def run_reference(args, rank, world):
     w, y, _ = workload(args, "cuda" if _cuda() else "cpu")
     cores = oracle.set_threads(0)
     n = w.n
-    rows_per_step = min(n, 4000)
+    rows_per_step = min(n, 2000)
     rng = np.random.default_rng(args.seed + 1)
+    ip, ix, vv = (np.ascontiguousarray(w.indptr), np.ascontiguousarray(w.indices),
+                  np.ascontiguousarray(w.values, dtype=np.float64))
     t0 = time.time()
-    oracle.bh_rows(y, None, None, None, args.theta, 1.0, 1.0, np.zeros(0, np.int64))
+    tree = oracle.PreparedTree(y)
     t_tree = time.time() - t0
     times = []
     for s in range(args.warmup + args.steps):
         rows = rng.choice(n, size=rows_per_step, replace=False)
         t0 = time.time()
-        oracle.bh_rows(y, w.indptr, w.indices, w.values, args.theta, 1.0, 1.0, rows)
+        tree.walk_rows(rows, ip, ix, vv, args.theta, 1.0, 1.0)
         dt = time.time() - t0
         if s >= args.warmup:
             times.append(dt)
+    tree.close()
     t_s = float(np.mean(times))
-    t_full = t_tree + (n / rows_per_step) * max(t_s - t_tree, 1e-9)
+    t_full = t_tree + (n / rows_per_step) * t_s
     value = 1.0 / t_full
-    sample = (f"per step: oracle tree build over all {n} points + BH walk and attraction for {rows_per_step} "
-              f"random rows; iteration time extrapolated as t_tree + (N/rows)(t_step - t_tree), "
-              f"t_tree={t_tree:.2f}s t_step={t_s:.2f}s")
+    sample = (f"oracle tree (literal insertion) built once over all {n} points ({t_tree:.2f} s); each step "
+              f"walks {rows_per_step} random rows (BH repulsion + attraction, {t_s * 1e3:.1f} ms); "
+              f"iteration time = t_tree + (N / rows) t_step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -245,12 +263,18 @@ def run_ours(args, rank, world, local):
     t.set_P(w.indptr, w.indices, w.values)
     t.set_Y(y)
     g32, z32 = t.grad(theta, 1.0)            # gradient at the start state (error gate)
-    t.set_counters(True)
-    t.grad(theta, 1.0)
-    cnt = t.get_counters()
-    t.set_counters(False)
-    acc, pairs, visits, queries = [int(v) for v in cnt[:4]]
     t.step(args.warmup, theta, 1.0, lr, 0.8)
+    y_s = t.get_Y()                           # start of the timed segment
+    v_s, _, _ = t.get_state()
+    if args.profile_only:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t.step(args.steps, theta, 1.0, lr, 0.8)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "n": n, "steps": args.steps,
+                              "ms_per_step": (time.perf_counter() - t0) * 1e3 / args.steps}), flush=True)
+        return
     t.set_profiling(True)
     t.get_profile()
     launches0 = int(t.get_counters()[4])
@@ -271,21 +295,56 @@ def run_ours(args, rank, world, local):
     ms_per_step = ms / args.steps
     value = args.steps * world / (ms / 1e3)
 
+    # ---- the same segment again with the counting walk (deterministic replay)
+    t.set_Y(y_s)
+    t.set_state(v_s, None, 0)
+    t.set_counters(True)
+    t.step(args.steps, theta, 1.0, lr, 0.8)
+    cnt = t.get_counters()
+    t.set_counters(False)
+    acc, pairs, visits, queries = [int(v) for v in cnt[:4]]
+    y_end = t.get_Y()
+
     # ---- roofline of the dominant kernel (tree walk) --------------------
     walk_ms = prof["walk"] / max(piters, 1)
-    lane_visits = visits * 32  # upper bound of criterion evaluations: every lane of each warp visit
-    flops = acc * FLOPS_PAIR + pairs * (FLOPS_PAIR + FLOPS_CRITERION) + lane_visits * FLOPS_CRITERION
+    lane_visits = visits * 32  # criterion evaluations bounded by every lane of each warp visit
+    flops = (acc * FLOPS_PAIR + pairs * (FLOPS_PAIR + FLOPS_CRITERION) + lane_visits * FLOPS_CRITERION) / args.steps
     sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     achieved = flops / (walk_ms * 1e-3) / 1e12
     dominant = max(prof, key=prof.get)
 
-    # ---- FP64 GPU path ----------------------------------------------------
+    # ---- end to end through the C ABI, all iteration state in host memory -
+    k_e2e = max(3, min(args.steps, 20))
+    yh = torch.from_numpy(np.ascontiguousarray(y_s)).pin_memory()
+    vh = torch.from_numpy(np.ascontiguousarray(v_s)).pin_memory()
+    yv, vv = yh.numpy(), vh.numpy()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        t.set_Y(yh)
+        t.set_state(vv, None, 0)
+        t.step(1, theta, 1.0, lr, 0.8)
+        t.get_Y(yv)
+        v_now, _, _ = t.get_state()
+        vv[...] = v_now
+    torch.cuda.synchronize()
+    barrier(world)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": k_e2e * world / dt, "unit": UNIT, "steps": k_e2e,
+           "h2d_bytes_per_step": int(yh.numel() * 8 + vh.numel() * 8),
+           "d2h_bytes_per_step": int(yh.numel() * 8 + vh.numel() * 8),
+           "call": "per step: hts_set_Y + hts_set_state (host Y, velocity) -> hts_step(1) -> hts_get_Y + "
+                   "hts_get_state (host); same trajectory as the device-resident timed steps"}
+    t.close()
+
+    # ---- FP64 GPU path on the same segment --------------------------------
     k64 = args.fp64_steps or max(3, args.steps // 10)
     t64 = HyperbolicTSNE(precision="fp64", device=local)
     t64.set_P(w.indptr, w.indices, w.values)
-    t64.set_Y(y)
-    t64.step(1, theta, 1.0, lr, 0.8)
+    t64.set_Y(y_s)
+    t64.set_state(v_s, None, 0)
     barrier(world)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -296,30 +355,10 @@ def run_ours(args, rank, world, local):
     value64 = k64 * world / (ms64 / 1e3)
     t64.close()
 
-    # ---- end to end through the C ABI with host buffers -------------------
-    k_e2e = max(3, min(args.steps, 20))
-    yh = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
-    yo = torch.empty_like(yh).pin_memory()
-    t.step(1, theta, 1.0, lr, 0.8)
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        t.set_Y(yh)
-        t.step(1, theta, 1.0, lr, 0.8)
-        t.get_Y(yo)
-    torch.cuda.synchronize()
-    barrier(world)
-    dt = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": k_e2e * world / dt, "unit": UNIT, "h2d_bytes_per_step": int(yh.numel() * 8),
-           "d2h_bytes_per_step": int(yo.numel() * 8),
-           "call": "hts_set_Y(host) + hts_step(1) + hts_get_Y(host) per step, pinned host buffers"}
-    t.close()
-
     # ---- oracle: error gate and CPU baseline (rank 0 only) ---------------
     err = None
     cpu = None
-    if rank == 0 and world >= 1 and not args.no_oracle:
+    if rank == 0 and not args.no_oracle:
         rng = np.random.default_rng(args.seed + 2)
         rows = np.sort(rng.choice(n, size=min(args.sample_rows, n), replace=False))
         ref, t_or, cores = oracle_pass(w, y, theta, rows)
@@ -332,31 +371,35 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return
+    r_end = np.linalg.norm(y_end, axis=1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"single-cell-like N={n} D=50 (200 Zipf clusters, log-normal), kNN k=90 perplexity "
                                f"30, FP32 CSR, theta={theta}, FP32-mixed", "n": n, "nnz": int(w.nnz),
-                   "theta": theta, "precision": "fp32_mixed", "y_state": "synthetic spread (mid-run-like)",
+                   "theta": theta, "precision": "fp32_mixed",
+                   "steps_protocol": "exaggeration 1, momentum 0.8, lr = N/12000",
+                   "y_state": "synthetic spread (mid-run-like) + warmup steps",
                    "l2": "inputs larger than L2 (CSR ~%.2f GB)" % (w.nnz * 8 / 1e9),
                    "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
         "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
                      "fp32_mixed_speedup": value / value64},
         "grad_rel_err": err,
         "phase_ms_per_step": {k: v / max(piters, 1) for k, v in prof.items()},
-        "walk_counters": {"accepted_cells": acc, "leaf_pairs": pairs, "warp_node_visits": visits,
-                          "queries": queries,
-                          "interactions_per_point": (acc + pairs) / max(queries, 1)},
+        "walk_counters_per_step": {"accepted_cells": acc / args.steps, "leaf_pairs": pairs / args.steps,
+                                   "warp_node_visits": visits / args.steps,
+                                   "interactions_per_point": (acc + pairs) / max(queries, 1)},
         "roofline": {"kernel": "walk_f32_kernel (BH tree walk)", "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                     "dominant_phase": dominant,
+                     "dominant_phase": dominant, "walk_ms": walk_ms,
                      "peak_basis": "FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (sampled SM clock)" % (
                          props.multi_processor_count, sm_mhz)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
+        "y_end": {"max_radius": float(r_end.max()), "frac_within_1e-4_of_rim": float(np.mean(r_end > 1 - 1e-4))},
     }
     print(json.dumps(line), flush=True)
 

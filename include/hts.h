@@ -179,10 +179,11 @@ HTS_API int hts_get_keys(hts_ctx *ctx, uint64_t *keys_out, double *bounds_out, i
 HTS_API int hts_get_tree(hts_ctx *ctx, int64_t cap, int64_t *count_out, int32_t *depth, uint64_t *prefix,
                  int64_t *count, int64_t *first, double *ycell, double *rcell);
 
-/* Counters (host int64[5]): [0..3] of the last tree walk -- accepted cells,
- * leaf pair interactions, warp node visits, query points -- filled only
- * while hts_set_counters(ctx, 1) is on (the walk then runs a counting
- * variant); [4] the number of CUDA kernels this context has launched. */
+/* Counters (host int64[5]): [0..3] summed over the tree walks run while
+ * counting is on -- accepted cells, leaf pair interactions, warp node
+ * visits, query points (the walk then runs a counting variant; switching
+ * counting on resets them); [4] the number of CUDA kernels this context
+ * has launched. */
 HTS_API int hts_get_counters(hts_ctx *ctx, int64_t *out5);
 HTS_API int hts_set_counters(hts_ctx *ctx, int enable);
 

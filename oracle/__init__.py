@@ -69,6 +69,9 @@ def _load():
                                       vp, vp]),
                 "ho_bh_rows": (None, [i64, vp, vp, vp, vp, d, d, i32, i32, d, i64, vp, vp, vp]),
                 "ho_kl": (d, [i64, vp, vp, vp, vp, d, i32]),
+                "ho_bh_prepare": (vp, [i64, vp, i32]),
+                "ho_bh_release": (None, [vp]),
+                "ho_bh_walk_rows": (None, [vp, vp, vp, vp, vp, d, d, i32, d, i64, vp, vp]),
                 "ho_step": (None, [i64, vp, vp, vp, vp, vp, vp, i32, d, d, d, d, i32, i32, i32, d,
                                    i32]),
             }
@@ -239,6 +242,34 @@ def bh_rows(y, indptr, indices, values, theta, exag, Z, rows, split_rule: int = 
     _load().ho_bh_rows(y.shape[0], _p(y), _p(ip), _p(ix), _p(vv), float(theta), float(exag),
                        int(split_rule), int(grad_form), float(Z), r.shape[0], _p(r), _p(g), _p(fz))
     return g, fz
+
+
+class PreparedTree:
+    """Oracle tree built once (literal insertion) for repeated row walks."""
+
+    def __init__(self, y, split_rule: int = 0):
+        self.y = _f64(y).reshape(-1, 2)
+        self._h = C.c_void_p(_load().ho_bh_prepare(self.y.shape[0], _p(self.y), int(split_rule)))
+
+    def walk_rows(self, rows, indptr=None, indices=None, values=None, theta=0.5, exag=1.0, Z=1.0,
+                  grad_form: int = 0):
+        ip, ix, vv = _csr(indptr, indices, values)
+        r = np.ascontiguousarray(rows, dtype=np.int64)
+        g = np.zeros((r.shape[0], 2))
+        _load().ho_bh_walk_rows(self._h, _p(self.y), _p(ip), _p(ix), _p(vv), float(theta), float(exag),
+                                int(grad_form), float(Z), r.shape[0], _p(r), _p(g))
+        return g
+
+    def close(self):
+        if self._h:
+            _load().ho_bh_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def step(y, v, indptr, indices, values, n_iter: int, theta: float, exag: float, lr: float,

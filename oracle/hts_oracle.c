@@ -826,6 +826,31 @@ void ho_bh_rows(int64_t n, const double *y, const int64_t *indptr, const int32_t
     tree_free(t);
 }
 
+/* A tree built once and walked for many row samples (timing of the oracle
+ * on bounded samples).  Same arithmetic as ho_bh_rows. */
+void *ho_bh_prepare(int64_t n, const double *y, int split_rule) { return tree_build_insert(n, y, split_rule); }
+
+void ho_bh_release(void *t) { tree_free((otree *)t); }
+
+void ho_bh_walk_rows(void *tp, const double *y, const int64_t *indptr, const int32_t *indices,
+                     const double *vals, double theta, double exag, int grad_form, double Z, int64_t nrows,
+                     const int64_t *rows, double *g)
+{
+    const otree *t = (const otree *)tp;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        bh_acc a = {0, 0, 0, 0, 0, 0};
+        bh_visit(t, y, 0, i, theta, grad_form, &a);
+        double fa[2] = {0, 0};
+        if (indptr) attraction_row(i, y, indptr, indices, vals, grad_form, fa);
+        if (g) {
+            g[2 * r] = 4.0 * (exag * fa[0] - a.fx / Z);
+            g[2 * r + 1] = 4.0 * (exag * fa[1] - a.fy / Z);
+        }
+    }
+}
+
 /* KL cost with the BH normalisation (theta > 0) or the exact one (theta == 0). */
 double ho_kl(int64_t n, const double *y, const int64_t *indptr, const int32_t *indices,
              const double *vals, double theta, int split_rule)

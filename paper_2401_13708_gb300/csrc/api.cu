@@ -653,6 +653,9 @@ int hts_get_tree(hts_ctx *c, int64_t cap, int64_t *count_out, int32_t *depth, ui
 int hts_set_counters(hts_ctx *c, int enable)
 {
     if (!c) return HTS_EINVAL;
+    int r = set_device(c);
+    if (r) return r;
+    if (enable && !c->counters_on) CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream));
     c->counters_on = enable ? 1 : 0;
     return HTS_OK;
 }

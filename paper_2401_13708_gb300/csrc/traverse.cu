@@ -331,8 +331,7 @@ void launch_walk(hts_ctx *c)
     const int n = (int)c->n;
     const int warps = (n + 31) / 32;
     const int blocks = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
-    const bool cnt = c->counters_on != 0;
-    if (cnt) cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream);
+    const bool cnt = c->counters_on != 0;  // counters accumulate while enabled
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
 #define HTS_WALK(GF, CT) \
