@@ -135,7 +135,7 @@ int ensure_points(hts_ctx *c, int64_t n)
     AL(c->sort_counts, (size_t)(256 * tiles));
     c->scan_tmp_len = scan_tmp_size(std::max<int64_t>(256 * tiles, (int64_t)N + 1));
     AL(c->scan_tmp, (size_t)c->scan_tmp_len);
-    AL(c->red_tmp, 3 * ((size_t)N * 32 / 256 + 2));
+    AL(c->red_tmp, std::max<size_t>(3 * ((size_t)N * 32 / 256 + 2), 512));
 #undef AL
     c->n_nodes = c->pre + n;
     c->cap_n = n;

@@ -28,18 +28,33 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
     const float twoil = 2.0f * q.il;
     const int64_t e0 = indptr[row], e1 = indptr[row + 1];
     float ax = 0.f, ay = 0.f, as = 0.f;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-        const int j = __ldg(indices + e);
-        const float pv = __ldg(vals + e);
-        const PointF o = pts[j];
-        float dx = (q.xh - o.xh) + (q.xl - o.xl);
-        float dy = (q.yh - o.yh) + (q.yl - o.yl);
-        float s = fmaf(dx, dx, dy * dy);
-        PairF t = pair_terms_f32<GF>(s * twoil * o.il);
-        float k = pv * t.att * o.il;
-        ax = fmaf(k, dx, ax);
-        ay = fmaf(k, dy, ay);
-        as = fmaf(k, s, as);
+    // four entries per lane per pass: the index loads and the gathers they feed
+    // are issued before any arithmetic, so four misses overlap
+    constexpr int U = 4;
+    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
+        int j[U];
+        float pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t eu = e + 32 * u;
+            const bool ok = eu < e1;
+            j[u] = ok ? __ldg(indices + eu) : row;
+            pv[u] = ok ? __ldg(vals + eu) : 0.0f;
+        }
+        PointF o[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) o[u] = pts[j[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float dx = (q.xh - o[u].xh) + (q.xl - o[u].xl);
+            float dy = (q.yh - o[u].yh) + (q.yl - o[u].yl);
+            float s = fmaf(dx, dx, dy * dy);
+            PairF t = pair_terms_f32<GF>(s * twoil * o[u].il);
+            float k = pv[u] * t.att * o[u].il;
+            ax = fmaf(k, dx, ax);
+            ay = fmaf(k, dy, ay);
+            as = fmaf(k, s, as);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         ax += __shfl_xor_sync(0xffffffffu, ax, o);

@@ -32,6 +32,11 @@ namespace {
 constexpr int kWalkBlock = 256;
 constexpr int kExactBlock = 256;
 
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int k)
 {
     const float4 *p = reinterpret_cast<const float4 *>(nodes + k);
@@ -70,6 +75,9 @@ __global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF
     unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
     while (node < m) {
         const NodeF c = load_node(nodes, node);
+        // the next node is node + 1 or c.skip: start pulling the far one into L1
+        // now so its latency overlaps this node's work
+        if (lane == 0 && c.skip < m) prefetch_l1(nodes + c.skip);
         const bool active = node >= resume;
         int next = node + 1;
         if (c.count >= 2) {

@@ -1,7 +1,7 @@
 // update.cu -- Z, the gradient and the Riemannian step, all in float64.
 //
-// reduce_z   Z = sum_i Z_i in a fixed order (one block, strided partial sums
-//            then a shared-memory tree), so the value is reproducible.
+// reduce_z   Z = sum_i Z_i in a fixed order (256 fixed block partials, then
+//            one block), so the value is reproducible.
 // update     g_i = 4 (exag F_attr,i - F_rep,i / Z)  (Eq. KlGradientHyperbolicSplit
 //            with the exaggeration of Sec. 5.1), then
 //              r_i = lambda_i^-metric_pow g_i  ("product of lambda^-1 with the
@@ -20,14 +20,30 @@ namespace {
 
 constexpr int kBlock = 256;
 
-__global__ void reduce_sum_kernel(int n, const double *__restrict__ v, double *out)
+// Fixed-shape two-pass sum: kRedBlocks blocks reduce grid-strided slices,
+// one block adds the partials in order -- reproducible for a given n.
+constexpr int kRedBlocks = 256;
+
+__global__ void __launch_bounds__(kBlock) partial_sum_kernel(int n, const double *__restrict__ v, double *partial)
 {
-    __shared__ double sh[1024];
+    __shared__ double sh[kBlock];
     double a = 0;
-    for (int k = threadIdx.x; k < n; k += 1024) a += v[k];
+    for (int k = blockIdx.x * kBlock + threadIdx.x; k < n; k += kRedBlocks * kBlock) a += v[k];
     sh[threadIdx.x] = a;
     __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
+    for (int s = kBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kRedBlocks) final_sum_kernel(const double *__restrict__ partial, double *out)
+{
+    __shared__ double sh[kRedBlocks];
+    sh[threadIdx.x] = partial[threadIdx.x];
+    __syncthreads();
+    for (int s = kRedBlocks / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
         __syncthreads();
     }
@@ -112,8 +128,10 @@ __global__ void check_y_kernel(int n, const double2 *__restrict__ y, int *status
 
 void launch_reduce_z(hts_ctx *c)
 {
-    reduce_sum_kernel<<<1, 1024, 0, c->stream>>>((int)c->n, c->zi, c->dscal);
-    c->launches += 1;
+    double *partial = c->red_tmp;  // >= kRedBlocks doubles
+    partial_sum_kernel<<<kRedBlocks, kBlock, 0, c->stream>>>((int)c->n, c->zi, partial);
+    final_sum_kernel<<<1, kRedBlocks, 0, c->stream>>>(partial, c->dscal);
+    c->launches += 2;
 }
 
 void launch_update(hts_ctx *c, double exag, double lr, double mom, double2 *g_out, int do_step)
