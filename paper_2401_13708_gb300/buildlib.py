@@ -23,6 +23,11 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 
+# float32 kernels: flush denormals so rsqrt / log2 / rcp are single
+# special-function operations (values below 1e-30 are clamped anyway)
+PER_FILE = {"traverse.cu": ["-ftz=true"], "attract.cu": ["-ftz=true"]}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -53,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

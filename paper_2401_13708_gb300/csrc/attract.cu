@@ -28,9 +28,9 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
     const float twoil = 2.0f * q.il;
     const int64_t e0 = indptr[row], e1 = indptr[row + 1];
     float ax = 0.f, ay = 0.f, as = 0.f;
-    // four entries per lane per pass: the index loads and the gathers they feed
-    // are issued before any arithmetic, so four misses overlap
-    constexpr int U = 4;
+    // eight entries per lane per pass: the index loads and the gathers they
+    // feed are issued before any arithmetic, so eight misses overlap
+    constexpr int U = 8;
     for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
         int j[U];
         float pv[U];

@@ -32,6 +32,8 @@
 //                 turns the criterion r_cell / d < theta into delta > thr.
 #include <math.h>
 
+#include <cuda/atomic>
+
 #include "hts_internal.cuh"
 
 namespace hts {
@@ -122,9 +124,10 @@ __global__ void bottom_up_kernel(int n, const double *__restrict__ terms, const 
     int node = leaf_parent[j];
     // The walk climbs at most n - 1 nodes; the bound only guards corrupt input.
     for (int guard = 0; node >= 0 && guard < n; ++guard) {
-        __threadfence();
-        if (atomicAdd(&flags[node], 1) == 0) return;  // first arrival: sibling not done yet
-        __threadfence();
+        // acquire-release: this thread's stored sums are visible to whoever
+        // arrives second, and the second arrival sees its sibling's sums
+        cuda::atomic_ref<int, cuda::thread_scope_device> flag(flags[node]);
+        if (flag.fetch_add(1, cuda::memory_order_acq_rel) == 0) return;  // first arrival
         DD a[3], b[3];
         load_child(left[node], terms, sums, a);
         load_child(right[node], terms, sums, b);
@@ -199,6 +202,55 @@ __device__ double cell_size(double lo, double hi, uint64_t a, int ell, int rule)
     return fmax(fmax(diag, radial), arc);
 }
 
+// Float32 version of the cell size and acceptance threshold, used when the
+// tree serves the float32 walk (its thresholds are float32 anyway).  The
+// radii, their gap and the conformal terms 1 - r^2 are formed in float64;
+// the distances use the float32 acosh of pair_terms_f32 (series below 0.1).
+__device__ __forceinline__ float acosh1p_f32(float delta)
+{
+    delta = fmaxf(delta, 0.0f);
+    const float x = delta * (delta + 2.0f);
+    const float t = sqrtf(x);
+    float fs = -8.0f / 693.0f;
+    fs = fmaf(fs, delta, 8.0f / 315.0f);
+    fs = fmaf(fs, delta, -2.0f / 35.0f);
+    fs = fmaf(fs, delta, 2.0f / 15.0f);
+    fs = fmaf(fs, delta, -1.0f / 3.0f);
+    fs = fmaf(fs, delta, 1.0f);
+    return delta < 0.1f ? t * fs : __logf(1.0f + delta + t);
+}
+
+__device__ float cell_threshold_f32(double lo, double hi, uint64_t a, int ell, int rule, double theta)
+{
+    double scale = ldexp(1.0, -ell);
+    double span = hi - lo;
+    double c0 = lo + span * ((double)a * scale);
+    double c1 = lo + span * ((double)(a + 1) * scale);
+    double dc = span * scale;
+    double r0 = radius_of(c0, rule), r1 = radius_of(c1, rule);
+    double dr = rule == HTS_EQUAL_AREA ? (r0 + r1 > 0.0 ? 2.0 * dc / ((c0 + 1.0) * (c1 + 1.0) * (r0 + r1)) : 0.0)
+                                       : dc;
+    const float a0 = (float)((1.0 - r0) * (1.0 + r0)), a1 = (float)((1.0 - r1) * (1.0 + r1));
+    const float f0 = (float)r0, f1 = (float)r1, fdr = (float)dr;
+    const float sh = __sinf((float)(kTwoPi * scale) * 0.5f);
+    const float sh2 = sh * sh;
+    const float diag = acosh1p_f32(2.0f * (fdr * fdr + 4.0f * f0 * f1 * sh2) / (a0 * a1));
+    const float radial = acosh1p_f32(2.0f * (fdr * fdr) / (a0 * a1));
+    const float arc = acosh1p_f32(2.0f * (4.0f * f1 * f1 * sh2) / (a1 * a1));
+    const float rc = fmaxf(fmaxf(diag, radial), arc);
+    // cosh(rc / theta) - 1 = 2 sinh(x)^2 with x = rc / (2 theta); series below 0.5
+    const float x = rc / (float)(2.0 * theta);
+    float sx;
+    if (x < 0.5f) {
+        const float x2 = x * x;
+        sx = x * fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 5040.0f, 1.0f / 120.0f), 1.0f / 6.0f), 1.0f);
+    } else {
+        const float e = __expf(x);
+        sx = 0.5f * (e - 1.0f / e);
+    }
+    return 2.0f * sx * sx;
+}
+
 __device__ __forceinline__ uint64_t radial_index(uint64_t prefix, int ell)
 {
     uint64_t a = 0;
@@ -246,11 +298,19 @@ __global__ void emit_kernel(EmitArgs A)
         double lob = __longlong_as_double((long long)A.mm[0]);
         double hib = __longlong_as_double((long long)A.mm[1]);
         uint64_t prefix = ell > 0 ? (A.keys[lo] >> (2 * (kLevels - ell))) : 0ull;
-        double rc = ell > 0 ? cell_size(lob, hib, radial_index(prefix, ell), ell, A.rule) : HUGE_VAL;
-        double thr = HUGE_VAL;
-        if (A.theta > 0.0 && ell > 0) {
-            double sh = sinh(rc / (2.0 * A.theta));
-            thr = 2.0 * sh * sh;
+        // float64 geometry for the float64 walk and for exports; float32 otherwise
+        const bool geo64 = A.nodes64 != nullptr || A.ex.depth != nullptr;
+        double rc = HUGE_VAL, thr = HUGE_VAL;
+        float thr32 = INFINITY;
+        if (ell > 0 && geo64) {
+            rc = cell_size(lob, hib, radial_index(prefix, ell), ell, A.rule);
+            if (A.theta > 0.0) {
+                double sh = sinh(rc / (2.0 * A.theta));
+                thr = 2.0 * sh * sh;
+            }
+            thr32 = (float)thr;
+        } else if (ell > 0 && A.theta > 0.0) {
+            thr32 = cell_threshold_f32(lob, hib, radial_index(prefix, ell), ell, A.rule, A.theta);
         }
         int count = hi - lo + 1;
         bool bucket = ell == kLevels;
@@ -265,7 +325,7 @@ __global__ void emit_kernel(EmitArgs A)
             nd.xl = (float)(cx - (double)nd.xh);
             nd.yl = (float)(cy - (double)nd.yh);
             nd.il = (float)il;
-            nd.thr = bucket ? __int_as_float(lo) : (float)thr;
+            nd.thr = bucket ? __int_as_float(lo) : thr32;
             nd.count = bucket ? -count : count;
             nd.skip = skip;
             A.nodes32[pos] = nd;
