@@ -232,7 +232,7 @@ __device__ float cell_threshold_f32(double lo, double hi, uint64_t a, int ell, i
                                        : dc;
     const float a0 = (float)((1.0 - r0) * (1.0 + r0)), a1 = (float)((1.0 - r1) * (1.0 + r1));
     const float f0 = (float)r0, f1 = (float)r1, fdr = (float)dr;
-    const float sh = __sinf((float)(kTwoPi * scale) * 0.5f);
+    const float sh = sinpif(ldexpf(1.0f, -ell));  // sin(dphi / 2), dphi = 2 pi 2^-ell: relative accuracy
     const float sh2 = sh * sh;
     const float diag = acosh1p_f32(2.0f * (fdr * fdr + 4.0f * f0 * f1 * sh2) / (a0 * a1));
     const float radial = acosh1p_f32(2.0f * (fdr * fdr) / (a0 * a1));
