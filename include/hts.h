@@ -205,6 +205,42 @@ HTS_API int hts_set_state(hts_ctx *ctx, const double *vel, const double *gains, 
 /* Number of points n and non-zeros nnz currently set (either may be NULL). */
 HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);
 
+/* ---- allocation-free exact gradient ---------------------------------------
+ * The paper has no counterpart to this entry point; it is a service to
+ * callers that must not allocate device memory -- code that queues work while
+ * a CUDA graph is being captured, where cudaMalloc is not allowed, or a
+ * plug-in inside a framework or server whose own allocator owns the device
+ * memory budget.
+ *
+ * hts_exact_grad_noalloc computes what hts_grad computes with theta = 0 in
+ * HTS_FP64: g = 4 (exaggeration * F_attr - F_rep / Z) with the exact
+ * repulsion over all pairs, and Z.  It needs no context.  Every pointer is
+ * device memory of the current device: y (n x 2 float64), the CSR matrix
+ * (int64 indptr[n+1], int32 indices[nnz], float64 values[nnz], laid out as
+ * for hts_set_P; not validated, but out-of-range entries are skipped), g_out
+ * (n x 2 float64) and Z_out (one float64, may be NULL).  The work is queued
+ * on `stream` (a cudaStream_t; NULL = legacy default stream) and is complete
+ * in stream order; nothing is copied to the host.
+ *
+ * Work arrays live in one fixed file-scope device array sized for
+ * HTS_NOALLOC_MAX_N points (about 4.5 MB); every device that loads the
+ * library holds it until the process exits.  n > HTS_NOALLOC_MAX_N returns
+ * HTS_ETOOLARGE.  No cudaMalloc, cudaFree or allocating library call is
+ * made.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, which may make the driver load this library's
+ * device code on that device); make that first call before any stream
+ * capture.  All calls share the array and each call overwrites what it
+ * reads, so no clearing is needed between calls -- but calls whose kernels
+ * overlap on the GPU (other streams, other host threads on the same device)
+ * race on it: serialise them.
+ * Errors: HTS_EINVAL (negative sizes, NULL pointers, bad grad_form or
+ * exaggeration), HTS_ETOOLARGE, HTS_ECUDA (address lookup or launch failed). */
+#define HTS_NOALLOC_MAX_N 65536
+#define HTS_ETOOLARGE (-8) /* size beyond the fixed capacity of an allocation-free entry point */
+HTS_API int hts_exact_grad_noalloc(int64_t n, int64_t nnz, const double *y, const int64_t *indptr,
+                                   const int32_t *indices, const double *values, double exaggeration,
+                                   int grad_form, double *g_out, double *Z_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

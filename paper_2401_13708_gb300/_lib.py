@@ -22,7 +22,9 @@ ERRORS = {
     -5: "HTS_ECUDA",
     -6: "HTS_EOOM",
     -7: "HTS_ENUMERIC",
+    -8: "HTS_ETOOLARGE",
 }
+NOALLOC_MAX_N = 65536
 FP64, FP32_MIXED = 0, 1
 EQUAL_LENGTH, EQUAL_AREA = 0, 1
 EXACT_KL, PAPER_EQ = 0, 1
@@ -34,7 +36,7 @@ EXPORTS = [
     "hts_default_config", "hts_create", "hts_destroy", "hts_set_P", "hts_set_Y", "hts_step", "hts_get_Y",
     "hts_grad", "hts_kl", "hts_last_error", "hts_get_keys", "hts_get_tree", "hts_get_counters",
     "hts_set_counters", "hts_get_state", "hts_set_state", "hts_get_sizes", "hts_set_profiling",
-    "hts_get_profile",
+    "hts_get_profile", "hts_exact_grad_noalloc",
 ]
 
 
@@ -93,6 +95,7 @@ def load(path: str = LIB_PATH):
             "hts_get_sizes": (i32, [vp, vp, vp]),
             "hts_set_profiling": (i32, [vp, i32]),
             "hts_get_profile": (i32, [vp, vp, vp]),
+            "hts_exact_grad_noalloc": (i32, [i64, i64, vp, vp, vp, vp, d, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
