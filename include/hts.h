@@ -202,6 +202,17 @@ HTS_API int hts_get_profile(hts_ctx *ctx, double *ms6, int64_t *iters);
 HTS_API int hts_get_state(hts_ctx *ctx, double *vel, double *gains, int64_t *iters, int where);
 HTS_API int hts_set_state(hts_ctx *ctx, const double *vel, const double *gains, int64_t iters, int where);
 
+/* CO-SNE objective (Sec. 4.3): lambda1 KL + lambda2 H with
+ * H = (1/n) sum_i (|x_i|^2 - |y_i|^2)^2, x_i the high-dimensional points.
+ * With x_sqnorm (n doubles |x_i|^2, in `where` memory) set, hts_grad and
+ * hts_step use lambda1 g_KL,i - (4 lambda2 / n)(|x_i|^2 - |y_i|^2) y_i -- the
+ * derivative of that cost (the variation printed in the paper has the
+ * opposite sign on the second term).  x_sqnorm == NULL switches the term off.
+ * hts_kl still returns KL alone.  Set Y first; a later hts_set_Y with another
+ * n switches the term off.  Errors: HTS_ENOTSET, HTS_EINVAL, HTS_EDOMAIN
+ * (negative or non-finite |x|^2), HTS_EOOM, HTS_ECUDA. */
+HTS_API int hts_set_cosne(hts_ctx *ctx, double lambda1, double lambda2, const double *x_sqnorm, int where);
+
 /* Number of points n and non-zeros nnz currently set (either may be NULL). */
 HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);
 

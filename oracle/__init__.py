@@ -70,6 +70,9 @@ def _load():
                 "ho_bh_rows": (None, [i64, vp, vp, vp, vp, d, d, i32, i32, d, i64, vp, vp, vp]),
                 "ho_kl": (d, [i64, vp, vp, vp, vp, d, i32]),
                 "ho_bh_prepare": (vp, [i64, vp, i32]),
+                "ho_cosne_H": (d, [i64, vp, vp]),
+                "ho_cosne_grad": (None, [i64, vp, vp, d, d, vp, vp]),
+                "ho_step_cosne": (None, [i64, vp, vp, vp, vp, vp, i32, d, d, d, d, vp, d, d]),
                 "ho_bh_release": (None, [vp]),
                 "ho_bh_walk_rows": (None, [vp, vp, vp, vp, vp, d, d, i32, d, i64, vp, vp]),
                 "ho_step": (None, [i64, vp, vp, vp, vp, vp, vp, i32, d, d, d, d, i32, i32, i32, d,
@@ -285,3 +288,31 @@ def step(y, v, indptr, indices, values, n_iter: int, theta: float, exag: float, 
                     float(theta), float(exag), float(lr), float(momentum), int(split_rule),
                     int(grad_form), int(metric_pow), float(eps), int(use_gains))
     return y, v, gn
+
+
+# -- CO-SNE objective (Sec. 4.3) ----------------------------------------------
+
+def cosne_H(y, xsq) -> float:
+    y = _f64(y).reshape(-1, 2)
+    x = _f64(xsq)
+    return _load().ho_cosne_H(y.shape[0], _p(y), _p(x))
+
+
+def cosne_grad(y, xsq, l1, l2, g_kl):
+    """lambda1 g_KL - (4 lambda2 / n)(|x|^2 - |y|^2) y."""
+    y = _f64(y).reshape(-1, 2)
+    x = _f64(xsq)
+    gk = _f64(g_kl).reshape(-1, 2)
+    out = np.zeros_like(y)
+    _load().ho_cosne_grad(y.shape[0], _p(y), _p(x), float(l1), float(l2), _p(gk), _p(out))
+    return out
+
+
+def step_cosne(y, v, indptr, indices, values, n_iter, theta, exag, lr, momentum, xsq, l1, l2):
+    y = _f64(y).reshape(-1, 2).copy()
+    v = _f64(v).reshape(-1, 2).copy()
+    ip, ix, vv = _csr(indptr, indices, values)
+    x = _f64(xsq)
+    _load().ho_step_cosne(y.shape[0], _p(y), _p(v), _p(ip), _p(ix), _p(vv), int(n_iter), float(theta), float(exag),
+                          float(lr), float(momentum), _p(x), float(l1), float(l2))
+    return y, v

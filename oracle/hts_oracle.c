@@ -865,14 +865,41 @@ double ho_kl(int64_t n, const double *y, const int64_t *indptr, const int32_t *i
 /* Riemannian gradient step (Sec. 4.2 and Sec. 5.1)                           */
 /* ------------------------------------------------------------------------ */
 
-/* n_iter iterations of: g = gradient (exact when theta == 0, else BH);
- * r = lambda^-metric_pow g (R2); optional gains (R8); v = momentum v - lr gains r;
- * y = proj(exp_y(v)) (R9).  y, v, gains (nullable when use_gains == 0) are
- * updated in place. */
-void ho_step(int64_t n, double *y, double *v, double *gains, const int64_t *indptr,
-             const int32_t *indices, const double *vals, int n_iter, double theta, double exag,
-             double lr, double momentum, int split_rule, int grad_form, int metric_pow,
-             double eps, int use_gains)
+/* CO-SNE objective (Sec. 4.3): lambda1 KL + lambda2 H with
+ *   H = (1/n) sum_i (|x_i|^2 - |y_i|^2)^2.
+ * dH/dy_i = -(4/n)(|x_i|^2 - |y_i|^2) y_i, so the gradient is
+ *   lambda1 g_KL,i - (4 lambda2 / n)(|x_i|^2 - |y_i|^2) y_i
+ * (the variation printed in Sec. 4.3 carries the opposite sign; this is the
+ * derivative of the stated cost).  xsq[i] = |x_i|^2. */
+double ho_cosne_H(int64_t n, const double *y, const double *xsq)
+{
+    double h = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double t = xsq[i] - sq2(y[2 * i], y[2 * i + 1]);
+        h += t * t;
+    }
+    return n > 0 ? h / (double)n : 0.0;
+}
+
+void ho_cosne_grad(int64_t n, const double *y, const double *xsq, double l1, double l2, const double *gkl,
+                   double *g)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double t = xsq[i] - sq2(y[2 * i], y[2 * i + 1]);
+        double c = 4.0 * l2 / (double)n * t;
+        g[2 * i] = l1 * gkl[2 * i] - c * y[2 * i];
+        g[2 * i + 1] = l1 * gkl[2 * i + 1] - c * y[2 * i + 1];
+    }
+}
+
+/* n_iter iterations of: g = gradient (exact when theta == 0, else BH; with
+ * the CO-SNE term when xsq != NULL); r = lambda^-metric_pow g (R2); optional
+ * gains (R8); v = momentum v - lr gains r; y = proj(exp_y(v)) (R9).  y, v,
+ * gains (nullable when use_gains == 0) are updated in place. */
+static void step_impl(int64_t n, double *y, double *v, double *gains, const int64_t *indptr,
+                      const int32_t *indices, const double *vals, int n_iter, double theta, double exag,
+                      double lr, double momentum, int split_rule, int grad_form, int metric_pow, double eps,
+                      int use_gains, const double *xsq, double l1, double l2)
 {
     double *g = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
     for (int it = 0; it < n_iter; ++it) {
@@ -881,6 +908,7 @@ void ho_step(int64_t n, double *y, double *v, double *gains, const int64_t *indp
         else
             ho_bh_grad(n, y, indptr, indices, vals, theta, exag, split_rule, grad_form, 0, NULL,
                        g, NULL, NULL, NULL, NULL, NULL);
+        if (xsq) ho_cosne_grad(n, y, xsq, l1, l2, g, g);
         for (int64_t i = 0; i < n; ++i) {
             double *yi = y + 2 * i, *vi = v + 2 * i;
             double lam = ho_lambda(yi);
@@ -904,4 +932,21 @@ void ho_step(int64_t n, double *y, double *v, double *gains, const int64_t *indp
         }
     }
     free(g);
+}
+
+void ho_step(int64_t n, double *y, double *v, double *gains, const int64_t *indptr,
+             const int32_t *indices, const double *vals, int n_iter, double theta, double exag,
+             double lr, double momentum, int split_rule, int grad_form, int metric_pow,
+             double eps, int use_gains)
+{
+    step_impl(n, y, v, gains, indptr, indices, vals, n_iter, theta, exag, lr, momentum, split_rule, grad_form,
+              metric_pow, eps, use_gains, NULL, 1.0, 0.0);
+}
+
+void ho_step_cosne(int64_t n, double *y, double *v, const int64_t *indptr, const int32_t *indices,
+                   const double *vals, int n_iter, double theta, double exag, double lr, double momentum,
+                   const double *xsq, double l1, double l2)
+{
+    step_impl(n, y, v, NULL, indptr, indices, vals, n_iter, theta, exag, lr, momentum, 0, 0, 1, 1e-5, 0, xsq,
+              l1, l2);
 }

@@ -36,7 +36,7 @@ EXPORTS = [
     "hts_default_config", "hts_create", "hts_destroy", "hts_set_P", "hts_set_Y", "hts_step", "hts_get_Y",
     "hts_grad", "hts_kl", "hts_last_error", "hts_get_keys", "hts_get_tree", "hts_get_counters",
     "hts_set_counters", "hts_get_state", "hts_set_state", "hts_get_sizes", "hts_set_profiling",
-    "hts_get_profile", "hts_exact_grad_noalloc",
+    "hts_get_profile", "hts_exact_grad_noalloc", "hts_set_cosne",
 ]
 
 
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
             "hts_set_profiling": (i32, [vp, i32]),
             "hts_get_profile": (i32, [vp, vp, vp]),
             "hts_exact_grad_noalloc": (i32, [i64, i64, vp, vp, vp, vp, d, i32, vp, vp, vp]),
+            "hts_set_cosne": (i32, [vp, d, d, vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -120,6 +120,15 @@ class HyperbolicTSNE:
         self.n = n
         del keep
 
+    def set_cosne(self, lambda1: float = 1.0, lambda2: float = 0.0, x_sqnorm=None):
+        """CO-SNE term (|x_i|^2 per point); x_sqnorm=None switches it off."""
+        if x_sqnorm is None:
+            self._check(self._lib.hts_set_cosne(self._ctx, 1.0, 0.0, None, HOST))
+            return
+        p, w, keep = _arg(x_sqnorm, np.float64)
+        self._check(self._lib.hts_set_cosne(self._ctx, float(lambda1), float(lambda2), p, w))
+        del keep
+
     # -- iteration ----------------------------------------------------------
     def step(self, n_iter: int, theta: float, exaggeration: float, lr: float, momentum: float):
         self._check(self._lib.hts_step(self._ctx, int(n_iter), float(theta), float(exaggeration), float(lr),

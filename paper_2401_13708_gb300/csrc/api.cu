@@ -317,7 +317,7 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->bn_lo); dfree(&c->bn_hi); dfree(&c->bn_pref); dfree(&c->bn_flag); dfree(&c->bn_quad);
     dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
     dfree(&c->sort_counts); dfree(&c->scan_tmp); dfree(&c->red_tmp); dfree(&c->minmax);
-    dfree(&c->dscal); dfree(&c->status); dfree(&c->counters);
+    dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     for (int k = 0; k < c->event_slots * (kPhases + 1); ++k) cudaEventDestroy(c->events[k]);
     delete[] c->events;
@@ -430,6 +430,11 @@ int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
         }
     } else if (n > 0 && (r = check_device_ptr(c, y))) {
         return r;
+    }
+    if (c->xsq && n != c->n) {
+        dfree(&c->xsq);  // the per-point term no longer matches
+        c->cosne_l1 = 1.0;
+        c->cosne_l2 = 0.0;
     }
     if ((r = ensure_points(c, n))) return r;
     if (n > 0) {
@@ -717,6 +722,38 @@ int hts_set_state(hts_ctx *c, const double *vel, const double *gains, int64_t it
     if (gains && c->n) CK(cudaMemcpyAsync(c->gains, gains, sizeof(double2) * (size_t)c->n, k, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->iters = iters;
+    return HTS_OK;
+}
+
+int hts_set_cosne(hts_ctx *c, double lambda1, double lambda2, const double *x_sqnorm, int where)
+{
+    if (!c) return HTS_EINVAL;
+    c->err.clear();
+    if (!x_sqnorm) {
+        dfree(&c->xsq);
+        c->cosne_l1 = 1.0;
+        c->cosne_l2 = 0.0;
+        return HTS_OK;
+    }
+    if (!c->have_Y) return fail(c, HTS_ENOTSET, "hts_set_cosne: set Y first (the term is per point)");
+    if (!isfinite(lambda1) || !isfinite(lambda2) || (where != HTS_HOST && where != HTS_DEVICE))
+        return fail(c, HTS_EINVAL, "hts_set_cosne: invalid argument");
+    int r = set_device(c);
+    if (r) return r;
+    if (where == HTS_HOST) {
+        for (int64_t i = 0; i < c->n; ++i)
+            if (!(x_sqnorm[i] >= 0.0) || !isfinite(x_sqnorm[i]))
+                return fail(c, HTS_EDOMAIN, "hts_set_cosne: |x_i|^2 must be finite and >= 0");
+    } else if ((r = check_device_ptr(c, x_sqnorm))) {
+        return r;
+    }
+    if ((r = dalloc(c, &c->xsq, (size_t)std::max<int64_t>(c->n, 1)))) return r;
+    if (c->n > 0)
+        CK(cudaMemcpyAsync(c->xsq, x_sqnorm, sizeof(double) * (size_t)c->n,
+                           where == HTS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->cosne_l1 = lambda1;
+    c->cosne_l2 = lambda2;
     return HTS_OK;
 }
 

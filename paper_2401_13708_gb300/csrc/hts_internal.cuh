@@ -124,6 +124,10 @@ struct hts_ctx {
     int *n_nodes = nullptr;          // device scalar: number of tree nodes
     double *h_pinned = nullptr;      // 8 doubles of pinned host scratch
 
+    // CO-SNE term (Sec. 4.3): lambda1 KL + lambda2 (1/n) sum (|x|^2 - |y|^2)^2
+    double cosne_l1 = 1.0, cosne_l2 = 0.0;
+    double *xsq = nullptr;           // |x_i|^2, n doubles (nullptr: term off)
+
     // instrumentation
     int64_t launches = 0;            // kernels launched since creation
     int profiling = 0;               // record phase events every iteration

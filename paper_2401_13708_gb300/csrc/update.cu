@@ -12,6 +12,9 @@
 //              y_i <- proj(exp_{y_i}(v_i)),  exp_y(v) = y (+) tanh(lambda |v| / 2) v / |v|
 //                    with Moebius addition (+) (Sec. 4.2), proj of Eq.
 //                    HyperbolicProjection: radius 1 - eps once |y| >= 1 - eps/2.
+//            With the CO-SNE term on (Sec. 4.3), g_i becomes
+//              lambda1 g_i - (4 lambda2 / n)(|x_i|^2 - |y_i|^2) y_i,
+//            the derivative of lambda1 KL + (lambda2 / n) sum (|x|^2 - |y|^2)^2.
 //            A non-finite result sets bit 1 of the status word.
 #include "hts_internal.cuh"
 
@@ -59,6 +62,8 @@ struct UpdateArgs {
     int metric_pow, use_gains, do_step;
     double2 *g_out;
     int *status;
+    const double *xsq;  // CO-SNE |x_i|^2 (nullptr: off)
+    double l1, l2;
 };
 
 __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
@@ -68,13 +73,18 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
     const double Z = *A.Z;
     const double invZ = Z > 0.0 ? 1.0 / Z : 0.0;
     const double2 fa = A.fattr[i], fr = A.frep[i];
-    const double gx = 4.0 * (A.exag * fa.x - fr.x * invZ);
-    const double gy = 4.0 * (A.exag * fa.y - fr.y * invZ);
+    double gx = 4.0 * (A.exag * fa.x - fr.x * invZ);
+    double gy = 4.0 * (A.exag * fa.y - fr.y * invZ);
+    double2 p = A.y[i];
+    const double n2 = p.x * p.x + p.y * p.y;
+    if (A.xsq) {  // CO-SNE: lambda1 g_KL - (4 lambda2 / n)(|x|^2 - |y|^2) y
+        const double c = 4.0 * A.l2 / (double)A.n * (A.xsq[i] - n2);
+        gx = A.l1 * gx - c * p.x;
+        gy = A.l1 * gy - c * p.y;
+    }
     if (A.g_out) A.g_out[i] = make_double2(gx, gy);
     if (!A.do_step) return;
-    double2 p = A.y[i];
     double2 v = A.vel[i];
-    const double n2 = p.x * p.x + p.y * p.y;
     const double lam = 2.0 / (1.0 - n2);
     const double sc = A.metric_pow == 2 ? 1.0 / (lam * lam) : 1.0 / lam;
     double kx = 1.0, ky = 1.0;
@@ -153,6 +163,9 @@ void launch_update(hts_ctx *c, double exag, double lr, double mom, double2 *g_ou
     A.do_step = do_step;
     A.g_out = g_out;
     A.status = c->status;
+    A.xsq = c->xsq;
+    A.l1 = c->cosne_l1;
+    A.l2 = c->cosne_l2;
     update_kernel<<<(A.n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(A);
     c->launches += 1;
 }

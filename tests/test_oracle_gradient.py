@@ -164,3 +164,31 @@ def test_degenerate_inputs():
     assert ex["Z"] == pytest.approx(z01 + 4 * z02, rel=1e-14)
     one = oracle.exact_grad(np.array([[0.2, 0.1]]))
     assert one["Z"] == 0 and np.all(one["g"] == 0)
+
+
+def test_cosne_gradient_finite_difference():
+    # CO-SNE (Sec. 4.3): cost lambda1 KL + (lambda2 / n) sum (|x_i|^2 - |y_i|^2)^2.
+    # Central differences of that cost (H by plain numpy) against the oracle's
+    # gradient; the printed variation's sign would fail this check.
+    y, ip, ix, vv = small_problem(n=14, seed=5, scale=0.7)
+    n = y.shape[0]
+    xsq = np.random.default_rng(8).uniform(0.0, 0.5, n)
+    l1, l2 = 0.7, 3.0
+
+    def cost(yy):
+        H = np.mean((xsq - (yy ** 2).sum(1)) ** 2)
+        return l1 * oracle.kl(yy, ip, ix, vv, 0.0) + l2 * H
+
+    assert oracle.cosne_H(y, xsq) == pytest.approx(np.mean((xsq - (y ** 2).sum(1)) ** 2), rel=1e-14)
+    g = oracle.cosne_grad(y, xsq, l1, l2, oracle.exact_grad(y, ip, ix, vv)["g"])
+    h = 1e-6
+    fd = np.zeros_like(y)
+    for i in range(n):
+        for c in range(2):
+            yp, ym = y.copy(), y.copy()
+            yp[i, c] += h
+            ym[i, c] -= h
+            fd[i, c] = (cost(yp) - cost(ym)) / (2 * h)
+    assert np.linalg.norm(fd - g) / np.linalg.norm(g) < 1e-6
+    printed = l1 * oracle.exact_grad(y, ip, ix, vv)["g"] + 4 * l2 / n * (xsq - (y ** 2).sum(1))[:, None] * y
+    assert np.linalg.norm(fd - printed) / np.linalg.norm(g) > 1e-2
