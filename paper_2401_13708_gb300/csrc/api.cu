@@ -128,14 +128,14 @@ int ensure_points(hts_ctx *c, int64_t n)
     AL(c->bn_pref, N);
     AL(c->bn_flag, N);
     AL(c->bn_quad, N);
-    AL(c->bn_sum, 6 * N);
+    AL(c->bn_sum, 6 * (N + 1));  // double-double prefix sums (n + 1 entries)
     AL(c->cnt, N + 1);
     AL(c->pre, N + 1);
     const int64_t tiles = ((int64_t)N + 4095) / 4096;
     AL(c->sort_counts, (size_t)(256 * tiles));
     c->scan_tmp_len = scan_tmp_size(std::max<int64_t>(256 * tiles, (int64_t)N + 1));
     AL(c->scan_tmp, (size_t)c->scan_tmp_len);
-    AL(c->red_tmp, std::max<size_t>(3 * ((size_t)N * 32 / 256 + 2), 512));
+    AL(c->red_tmp, std::max<size_t>(3 * ((size_t)N * 32 / 256 + 2), 512));  // also >= 6 (N / 1024 + 2)
 #undef AL
     c->n_nodes = c->pre + n;
     c->cap_n = n;

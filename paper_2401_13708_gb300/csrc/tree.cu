@@ -9,11 +9,11 @@
 //                 trees", HPG 2012): one thread per internal node finds its
 //                 key range and split by binary search on common-prefix
 //                 lengths; equal keys are ordered by index.
-//  3. sums        bottom-up over the binary tree: the second thread to reach
-//                 a node adds its two children in fixed (left, right) order
-//                 in double-double, so every cell's sums are exact to ~1e-30
-//                 and independent of scheduling; rounding them once gives the
-//                 correctly rounded float64 sums.
+//  3. sums        exclusive prefix sums of the Einstein terms over the sorted
+//                 points, in double-double with a fixed combination order; a
+//                 cell's sums are P[hi + 1] - P[lo], accurate to ~2^-106 of the
+//                 largest prefix, so rounding them once gives the correctly
+//                 rounded float64 sums (and the oracle's midpoints).
 //  4. quad nodes  a binary node is a quadtree cell iff its quad level
 //                 floor(prefix_bits / 2) exceeds its parent's; that is the
 //                 deepest cell of a chain of one-child cells (chains collapse:
@@ -23,7 +23,8 @@
 //  5. layout      nodes in pre-order (children in key order): order by first
 //                 point, then by depth, so per first point p the count of
 //                 nodes starting at p is scanned into pre[]; a cell's position
-//                 is pre[lo] + (its ancestors starting at lo) and the index
+//                 is pre[lo] + (number of shallower cells starting at lo, a
+//                 popcount of a per-point bit set of quad levels) and the index
 //                 after its subtree is pre[hi + 1].
 //  6. emit        midpoint y_cell = m / (1 + sqrt(1 - |m|^2)), m = S_u / S_gamma,
 //                 il = 1 / (1 - |y_cell|^2), r_cell (longest internal distance:
@@ -100,50 +101,117 @@ __global__ void radix_tree_kernel(int n, const uint64_t *__restrict__ keys, int 
     if (i == 0) parent[0] = -1;
 }
 
-__device__ __forceinline__ void load_child(int c, const double *__restrict__ terms, const double *sums, DD out[3])
+// ---- exclusive prefix sums of the Einstein terms in double-double ----------
+// P[p] = sum of terms of sorted points 0 .. p-1 (three quantities), so the
+// sums of any cell [lo, hi] are P[hi + 1] - P[lo].  Fixed block shape and
+// fixed combination order: the result is reproducible; double-double keeps
+// the absolute error near 2^-106 of the largest prefix, far below one float64
+// ulp of any cell sum, so the cell sums round as the exact sums do.
+constexpr int kScanT = 256;            // threads per scan block
+constexpr int kScanI = 4;              // elements per thread
+constexpr int kScanB = kScanT * kScanI;
+
+struct DD3 {
+    DD g, x, y;
+};
+
+__device__ __forceinline__ DD3 dd3_add(const DD3 &a, const DD3 &b)
 {
-    if (c < 0) {
-        int p = ~c;
-        out[0] = DD{terms[3 * p], 0.0};
-        out[1] = DD{terms[3 * p + 1], 0.0};
-        out[2] = DD{terms[3 * p + 2], 0.0};
-    } else {
-        const double *s = sums + 6 * (size_t)c;
-        out[0] = DD{__ldcg(s + 0), __ldcg(s + 1)};
-        out[1] = DD{__ldcg(s + 2), __ldcg(s + 3)};
-        out[2] = DD{__ldcg(s + 4), __ldcg(s + 5)};
-    }
+    return DD3{dd_add(a.g, b.g), dd_add(a.x, b.x), dd_add(a.y, b.y)};
 }
 
-__global__ void bottom_up_kernel(int n, const double *__restrict__ terms, const int *__restrict__ left,
-                                 const int *__restrict__ right, const int *__restrict__ parent,
-                                 const int *__restrict__ leaf_parent, int *flags, double *sums)
+__device__ __forceinline__ DD3 dd3_zero() { return DD3{{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}}; }
+
+__device__ __forceinline__ DD3 dd3_shfl_up(const DD3 &v, int o)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n || n < 2) return;
-    int node = leaf_parent[j];
-    // The walk climbs at most n - 1 nodes; the bound only guards corrupt input.
-    for (int guard = 0; node >= 0 && guard < n; ++guard) {
-        // acquire-release: this thread's stored sums are visible to whoever
-        // arrives second, and the second arrival sees its sibling's sums
-        cuda::atomic_ref<int, cuda::thread_scope_device> flag(flags[node]);
-        if (flag.fetch_add(1, cuda::memory_order_acq_rel) == 0) return;  // first arrival
-        DD a[3], b[3];
-        load_child(left[node], terms, sums, a);
-        load_child(right[node], terms, sums, b);
-        double *s = sums + 6 * (size_t)node;
+    DD3 r;
+    r.g.hi = __shfl_up_sync(0xffffffffu, v.g.hi, o);
+    r.g.lo = __shfl_up_sync(0xffffffffu, v.g.lo, o);
+    r.x.hi = __shfl_up_sync(0xffffffffu, v.x.hi, o);
+    r.x.lo = __shfl_up_sync(0xffffffffu, v.x.lo, o);
+    r.y.hi = __shfl_up_sync(0xffffffffu, v.y.hi, o);
+    r.y.lo = __shfl_up_sync(0xffffffffu, v.y.lo, o);
+    return r;
+}
+
+// One block scans kScanB consecutive elements: out[i] = exclusive prefix within
+// the block, tot[block] = block total.  Input: raw terms (3 doubles per point)
+// when `terms` is given, otherwise DD3 values.
+__global__ void __launch_bounds__(kScanT) dd_scan_block_kernel(int len, const double *__restrict__ terms,
+                                                              const DD3 *__restrict__ in, DD3 *out, DD3 *tot)
+{
+    __shared__ DD3 wsum[kScanT / 32];
+    const int base = blockIdx.x * kScanB + threadIdx.x * kScanI;
+    DD3 v[kScanI];
+    DD3 t = dd3_zero();
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            DD r = dd_add(a[k], b[k]);
-            __stcg(s + 2 * k, r.hi);
-            __stcg(s + 2 * k + 1, r.lo);
+    for (int k = 0; k < kScanI; ++k) {
+        const int i = base + k;
+        if (i < len) {
+            if (terms) {
+                v[k] = DD3{{terms[3 * i], 0.0}, {terms[3 * i + 1], 0.0}, {terms[3 * i + 2], 0.0}};
+            } else {
+                v[k] = in[i];
+            }
+        } else {
+            v[k] = dd3_zero();
         }
-        node = parent[node];
+        t = dd3_add(t, v[k]);
     }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    DD3 inc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        DD3 u = dd3_shfl_up(inc, o);
+        if (lane >= o) inc = dd3_add(u, inc);
+    }
+    DD3 excl = dd3_shfl_up(inc, 1);
+    if (lane == 0) excl = dd3_zero();
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    DD3 woff = dd3_zero();
+    for (int k = 0; k < w; ++k) woff = dd3_add(woff, wsum[k]);
+    DD3 run = dd3_add(woff, excl);
+#pragma unroll
+    for (int k = 0; k < kScanI; ++k) {
+        const int i = base + k;
+        if (i < len) out[i] = run;
+        run = dd3_add(run, v[k]);
+    }
+    if (threadIdx.x == kScanT - 1) tot[blockIdx.x] = run;
 }
 
+__global__ void dd_scan_add_kernel(int len, DD3 *out, const DD3 *__restrict__ off)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = dd3_add(off[i / kScanB], out[i]);
+}
+
+// Exclusive scan of len elements into out[0 .. len-1]; the grand total goes to
+// *total.  tmp holds the block totals of every recursion level.
+void dd_scan(int len, const double *terms, const DD3 *in, DD3 *out, DD3 *total, DD3 *tmp, cudaStream_t s,
+             int64_t *launches)
+{
+    const int blocks = (len + kScanB - 1) / kScanB;
+    DD3 *tot = tmp;
+    dd_scan_block_kernel<<<blocks, kScanT, 0, s>>>(len, terms, in, out, tot);
+    *launches += 1;
+    if (blocks == 1) {
+        cudaMemcpyAsync(total, tot, sizeof(DD3), cudaMemcpyDeviceToDevice, s);
+        return;
+    }
+    dd_scan(blocks, nullptr, tot, tot, total, tmp + blocks, s, launches);
+    dd_scan_add_kernel<<<(len + 255) / 256, 256, 0, s>>>(len, out, tot);
+    *launches += 1;
+}
+
+// Quad levels present among the cells whose first sorted point is p, one bit
+// per level (cells with a common first point are nested, at distinct levels),
+// so a cell's rank among them is a popcount.  Points outside buckets are
+// leaves of their own.
 __global__ void quad_mark_kernel(int n, const int *__restrict__ parent, const int *__restrict__ leaf_parent,
-                                 const int *__restrict__ lo_arr, const int *__restrict__ pref, int *quad, int *cnt)
+                                 const int *__restrict__ lo_arr, const int *__restrict__ pref, int *quad,
+                                 unsigned *mask)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n - 1) {  // binary internal node k
@@ -151,11 +219,19 @@ __global__ void quad_mark_kernel(int n, const int *__restrict__ parent, const in
         int pl = k == 0 ? -1 : quad_level(pref[parent[k]]);
         int q = lv > pl;
         quad[k] = q;
-        if (q) atomicAdd(&cnt[lo_arr[k]], 1);
+        if (q) atomicOr(&mask[lo_arr[k]], 1u << lv);
     }
-    if (k < n) {  // point k: a node of its own unless it sits in a bucket
+}
+
+__global__ void count_kernel(int n, const int *__restrict__ leaf_parent, const int *__restrict__ pref,
+                             const unsigned *__restrict__ mask, int *cnt)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
         bool leaf = n == 1 || quad_level(pref[leaf_parent[k]]) < kLevels;
-        if (leaf) atomicAdd(&cnt[k], 1);
+        cnt[k] = __popc(mask[k]) + (leaf ? 1 : 0);
+    } else if (k == n) {
+        cnt[n] = 0;
     }
 }
 
@@ -268,7 +344,8 @@ struct EmitArgs {
     const PointF *spts32;
     const PointD *spts64;
     const int *left, *parent, *leaf_parent, *lo_arr, *hi_arr, *pref, *quad, *cnt, *pre;
-    const double *sums;
+    const unsigned *mask;
+    const DD3 *prefix;  // n + 1 exclusive prefix sums of the Einstein terms
     const unsigned long long *mm;
     NodeF *nodes32;
     NodeD *nodes64;
@@ -283,13 +360,14 @@ __global__ void emit_kernel(EmitArgs A)
     const int n = A.n;
     if (k < n - 1 && A.quad[k]) {
         int lo = A.lo_arr[k], hi = A.hi_arr[k];
-        int rank = 0;
-        for (int a = A.parent[k]; a >= 0 && A.lo_arr[a] == lo; a = A.parent[a]) rank += A.quad[a];
+        int ell = quad_level(A.pref[k]);
+        int rank = __popc(A.mask[lo] & ((1u << ell) - 1u));  // shallower cells starting at lo
         int pos = A.pre[lo] + rank;
         int skip = A.pre[hi + 1];
-        int ell = quad_level(A.pref[k]);
-        const double *s = A.sums + 6 * (size_t)k;
-        double sg = s[0], sux = s[2], suy = s[4];
+        const DD3 p1 = A.prefix[hi + 1], p0 = A.prefix[lo];
+        const double sg = dd_add(p1.g, DD{-p0.g.hi, -p0.g.lo}).hi;
+        const double sux = dd_add(p1.x, DD{-p0.x.hi, -p0.x.lo}).hi;
+        const double suy = dd_add(p1.y, DD{-p0.y.hi, -p0.y.lo}).hi;
         double mx = __ddiv_rn(sux, sg), my = __ddiv_rn(suy, sg);
         double sq = __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))));
         double cx = __ddiv_rn(mx, __dadd_rn(1.0, sq)), cy = __ddiv_rn(my, __dadd_rn(1.0, sq));
@@ -416,19 +494,20 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex)
     const int gp = (n + kBlock - 1) / kBlock;
     gather_kernel<<<gp, kBlock, 0, s>>>(n, c->idx, c->y, c->pts32, c->pts64, f32 ? c->spts32 : nullptr,
                                         f32 ? nullptr : c->spts64, c->terms);
-    c->launches += 3;  // gather, quad_mark, emit
+    c->launches += 4;  // gather, quad_mark, count, emit
+    DD3 *prefix = reinterpret_cast<DD3 *>(c->bn_sum);  // n + 1 entries
+    unsigned *mask = reinterpret_cast<unsigned *>(c->bn_flag);
+    cudaMemsetAsync(mask, 0, sizeof(unsigned) * (size_t)n, s);
     if (n > 1) {
         const int gi = (n - 1 + kBlock - 1) / kBlock;
         radix_tree_kernel<<<gi, kBlock, 0, s>>>(n, c->keys, c->bn_left, c->bn_right, c->bn_parent, c->leaf_parent,
                                                 c->bn_lo, c->bn_hi, c->bn_pref);
-        cudaMemsetAsync(c->bn_flag, 0, sizeof(int) * (size_t)(n - 1), s);
-        bottom_up_kernel<<<gp, kBlock, 0, s>>>(n, c->terms, c->bn_left, c->bn_right, c->bn_parent, c->leaf_parent,
-                                               c->bn_flag, c->bn_sum);
-        c->launches += 2;
+        c->launches += 1;
+        dd_scan(n, c->terms, nullptr, prefix, prefix + n, reinterpret_cast<DD3 *>(c->red_tmp), s, &c->launches);
+        quad_mark_kernel<<<gp, kBlock, 0, s>>>(n, c->bn_parent, c->leaf_parent, c->bn_lo, c->bn_pref, c->bn_quad,
+                                               mask);
     }
-    cudaMemsetAsync(c->cnt, 0, sizeof(int) * (size_t)(n + 1), s);
-    quad_mark_kernel<<<gp, kBlock, 0, s>>>(n, c->bn_parent, c->leaf_parent, c->bn_lo, c->bn_pref, c->bn_quad,
-                                           c->cnt);
+    count_kernel<<<(n + 1 + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, c->leaf_parent, c->bn_pref, mask, c->cnt);
     c->launches += scan_exclusive(c->cnt, c->pre, (int64_t)n + 1, c->scan_tmp, s);
     EmitArgs A;
     A.n = n;
@@ -448,7 +527,8 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex)
     A.quad = c->bn_quad;
     A.cnt = c->cnt;
     A.pre = c->pre;
-    A.sums = c->bn_sum;
+    A.mask = mask;
+    A.prefix = prefix;
     A.mm = c->minmax;
     A.nodes32 = f32 ? c->nodes32 : nullptr;
     A.nodes64 = f32 ? nullptr : c->nodes64;
