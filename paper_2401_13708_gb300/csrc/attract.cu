@@ -2,9 +2,10 @@
 // KlGradientHyperbolicSplit), the KL cost terms (Eq. KLDivergence) and
 // device-side validation of a CSR matrix.
 //
-// One warp per row of P: the 32 lanes read consecutive (index, value)
-// entries (coalesced 128-byte loads), gather the neighbours' 32-byte point
-// records (random, mostly L2 hits) and reduce three scalars by shuffles.
+// A group of lanes per row of P (8 in float32, a warp in float64) reads
+// consecutive (index, value) entries (coalesced), gathers the neighbours'
+// 32-byte point records (random, mostly L2 hits) and reduces three scalars
+// by shuffles.
 // Per point: F_attr,i = 4 il_i (A_Delta + il_i A_s y_i) with
 //   A_Delta = sum_j p_ij (w d / t)_ij il_j Delta_ij,  A_s = same with s_ij.
 // Bytes per non-zero: 4 (index) + 4 or 8 (value) + 32 (gathered record).
@@ -15,37 +16,41 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Float32 path: a group of kGroup lanes per row (kBlock / kGroup rows per
+// block), so short rows do not leave most of a warp idle; each lane keeps
+// kUnroll index loads and gathers in flight before its arithmetic.
+constexpr int kGroup = 8;
+constexpr int kUnroll = 4;
+
 template <int GF>
 __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_t *__restrict__ indptr,
                                                              const int32_t *__restrict__ indices,
                                                              const float *__restrict__ vals,
                                                              const PointF *__restrict__ pts, double2 *fattr)
 {
-    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    const PointF q = pts[row];
+    const int row = (blockIdx.x * kBlock + threadIdx.x) / kGroup;
+    const int lane = threadIdx.x & (kGroup - 1);
+    const bool live = row < n;
+    const int r = live ? row : n - 1;
+    const PointF q = pts[r];
     const float twoil = 2.0f * q.il;
-    const int64_t e0 = indptr[row], e1 = indptr[row + 1];
+    const int64_t e0 = indptr[r], e1 = live ? indptr[r + 1] : e0;
     float ax = 0.f, ay = 0.f, as = 0.f;
-    // eight entries per lane per pass: the index loads and the gathers they
-    // feed are issued before any arithmetic, so eight misses overlap
-    constexpr int U = 8;
-    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
-        int j[U];
-        float pv[U];
+    for (int64_t e = e0 + lane; e < e1; e += kGroup * kUnroll) {
+        int j[kUnroll];
+        float pv[kUnroll];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t eu = e + 32 * u;
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t eu = e + kGroup * u;
             const bool ok = eu < e1;
-            j[u] = ok ? __ldg(indices + eu) : row;
+            j[u] = ok ? __ldg(indices + eu) : r;
             pv[u] = ok ? __ldg(vals + eu) : 0.0f;
         }
-        PointF o[U];
+        PointF o[kUnroll];
 #pragma unroll
-        for (int u = 0; u < U; ++u) o[u] = pts[j[u]];
+        for (int u = 0; u < kUnroll; ++u) o[u] = pts[j[u]];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 0; u < kUnroll; ++u) {
             float dx = (q.xh - o[u].xh) + (q.xl - o[u].xl);
             float dy = (q.yh - o[u].yh) + (q.yl - o[u].yl);
             float s = fmaf(dx, dx, dy * dy);
@@ -56,12 +61,12 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
             as = fmaf(k, s, as);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = kGroup / 2; o > 0; o >>= 1) {
         ax += __shfl_xor_sync(0xffffffffu, ax, o);
         ay += __shfl_xor_sync(0xffffffffu, ay, o);
         as += __shfl_xor_sync(0xffffffffu, as, o);
     }
-    if (lane == 0) {
+    if (lane == 0 && live) {
         double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
         double il = (double)q.il;
         double asd = il * (double)as;
@@ -201,13 +206,16 @@ void launch_attract(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
+    const int blocks32 = (int)(((int64_t)n * kGroup + kBlock - 1) / kBlock);
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
         const float *v = (const float *)c->values;
         if (c->cfg.grad_form == HTS_EXACT_KL)
-            attract_f32_kernel<0><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32, c->fattr);
+            attract_f32_kernel<0><<<blocks32, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32,
+                                                                      c->fattr);
         else
-            attract_f32_kernel<1><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32, c->fattr);
+            attract_f32_kernel<1><<<blocks32, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32,
+                                                                      c->fattr);
     } else {
         const double *v = (const double *)c->values;
         if (c->cfg.grad_form == HTS_EXACT_KL)

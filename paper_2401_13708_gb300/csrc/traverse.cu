@@ -24,12 +24,15 @@
 // written to the point's original index.
 #include <limits.h>
 
+#include <algorithm>
+
 #include "hts_internal.cuh"
 
 namespace hts {
 namespace {
 
 constexpr int kWalkBlock = 256;
+constexpr int kWalkBlocksPerSM = 8;  // 64 resident warps per SM at <= 32 registers
 constexpr int kExactBlock = 256;
 
 __device__ __forceinline__ void prefetch_l1(const void *p)
@@ -53,17 +56,15 @@ __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int 
     return r;
 }
 
+// One warp walks for the 32 sorted points of chunk `warp`.
 template <int GF, bool COUNT>
-__global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF *__restrict__ nodes,
-                                                              const int *__restrict__ n_nodes,
-                                                              const PointF *__restrict__ spts,
-                                                              const uint32_t *__restrict__ idx, double2 *frep,
-                                                              double *zi, unsigned long long *counters,
-                                                              int *status)
+__device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__restrict__ nodes,
+                                                const int *__restrict__ n_nodes,
+                                                const PointF *__restrict__ spts,
+                                                const uint32_t *__restrict__ idx, double2 *frep, double *zi,
+                                                unsigned long long *counters, int *status)
 {
-    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp * 32 >= n) return;
     const int p = warp * 32 + lane;
     const bool valid = p < n;
     const PointF q = spts[valid ? p : n - 1];
@@ -159,17 +160,38 @@ __global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF
     }
 }
 
+// Persistent grid: each warp takes the next chunk of 32 points from a global
+// counter until none are left, so uneven walks (dense regions) do not leave a
+// partly filled last wave of blocks.
 template <int GF, bool COUNT>
-__global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD *__restrict__ nodes,
+__global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF *__restrict__ nodes,
                                                               const int *__restrict__ n_nodes,
-                                                              const PointD *__restrict__ spts,
+                                                              const PointF *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              int *status)
+                                                              int *status, int *work)
 {
-    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp * 32 >= n) return;
+    const int chunks = (n + 31) >> 5;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(work, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= chunks) return;
+        walk_f32_chunk<GF, COUNT>(c, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
+    }
+}
+
+
+// One warp walks for the 32 sorted points of chunk `warp`.
+template <int GF, bool COUNT>
+__device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__restrict__ nodes,
+                                                const int *__restrict__ n_nodes,
+                                                const PointD *__restrict__ spts,
+                                                const uint32_t *__restrict__ idx, double2 *frep, double *zi,
+                                                unsigned long long *counters, int *status)
+{
+    const int lane = threadIdx.x & 31;
     const int p = warp * 32 + lane;
     const bool valid = p < n;
     const PointD q = spts[valid ? p : n - 1];
@@ -257,6 +279,29 @@ __global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD
     }
 }
 
+// Persistent grid: each warp takes the next chunk of 32 points from a global
+// counter until none are left, so uneven walks (dense regions) do not leave a
+// partly filled last wave of blocks.
+template <int GF, bool COUNT>
+__global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD *__restrict__ nodes,
+                                                              const int *__restrict__ n_nodes,
+                                                              const PointD *__restrict__ spts,
+                                                              const uint32_t *__restrict__ idx, double2 *frep,
+                                                              double *zi, unsigned long long *counters,
+                                                              int *status, int *work)
+{
+    const int lane = threadIdx.x & 31;
+    const int chunks = (n + 31) >> 5;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(work, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= chunks) return;
+        walk_f64_chunk<GF, COUNT>(c, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
+    }
+}
+
+
 // Exact repulsion: one thread per point i, tiles of 256 points j staged in
 // shared memory, every pair j != i.
 template <int GF>
@@ -338,13 +383,15 @@ void launch_walk(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int warps = (n + 31) / 32;
-    const int blocks = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
+    const int need = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
+    const int blocks = std::max(1, std::min(need, c->sm_count * kWalkBlocksPerSM));
     const bool cnt = c->counters_on != 0;  // counters accumulate while enabled
+    cudaMemsetAsync(c->work, 0, sizeof(int), c->stream);
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
 #define HTS_WALK(GF, CT) \
     walk_f32_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes32, c->n_nodes, c->spts32, c->idx, \
-                                                                  c->frep, c->zi, c->counters, c->status)
+                                                                  c->frep, c->zi, c->counters, c->status, c->work)
         if (c->cfg.grad_form == HTS_EXACT_KL) {
             if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
         } else {
@@ -354,7 +401,7 @@ void launch_walk(hts_ctx *c)
     } else {
 #define HTS_WALK(GF, CT) \
     walk_f64_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes64, c->n_nodes, c->spts64, c->idx, \
-                                                                  c->frep, c->zi, c->counters, c->status)
+                                                                  c->frep, c->zi, c->counters, c->status, c->work)
         if (c->cfg.grad_form == HTS_EXACT_KL) {
             if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
         } else {
