@@ -293,7 +293,7 @@ int hts_create(hts_ctx **out, const hts_config *cfg)
     }
     c->sm_count = prop.multiProcessorCount;
     if (dalloc(c, &c->minmax, 2) || dalloc(c, &c->dscal, 8) || dalloc(c, &c->status, 1) ||
-        dalloc(c, &c->counters, 4) || dalloc(c, &c->work, 1) || cudaMallocHost((void **)&c->h_pinned, 8 * sizeof(double)) != cudaSuccess) {
+        dalloc(c, &c->counters, 4) || cudaMallocHost((void **)&c->h_pinned, 8 * sizeof(double)) != cudaSuccess) {
         hts_destroy(c);
         return HTS_EOOM;
     }
@@ -317,7 +317,7 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->bn_lo); dfree(&c->bn_hi); dfree(&c->bn_pref); dfree(&c->bn_flag); dfree(&c->bn_quad);
     dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
     dfree(&c->sort_counts); dfree(&c->scan_tmp); dfree(&c->red_tmp); dfree(&c->minmax);
-    dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq); dfree(&c->work);
+    dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     for (int k = 0; k < c->event_slots * (kPhases + 1); ++k) cudaEventDestroy(c->events[k]);
     delete[] c->events;

@@ -122,7 +122,6 @@ struct hts_ctx {
     int *status = nullptr;
     unsigned long long *counters = nullptr;  // 4
     int *n_nodes = nullptr;          // device scalar: number of tree nodes
-    int *work = nullptr;             // device scalar: walk work counter
     double *h_pinned = nullptr;      // 8 doubles of pinned host scratch
 
     // CO-SNE term (Sec. 4.3): lambda1 KL + lambda2 (1/n) sum (|x|^2 - |y|^2)^2

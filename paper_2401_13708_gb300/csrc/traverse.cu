@@ -32,7 +32,6 @@ namespace hts {
 namespace {
 
 constexpr int kWalkBlock = 256;
-constexpr int kWalkBlocksPerSM = 8;  // 64 resident warps per SM at <= 32 registers
 constexpr int kExactBlock = 256;
 
 __device__ __forceinline__ void prefetch_l1(const void *p)
@@ -160,26 +159,19 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
     }
 }
 
-// Persistent grid: each warp takes the next chunk of 32 points from a global
-// counter until none are left, so uneven walks (dense regions) do not leave a
-// partly filled last wave of blocks.
+// One warp per chunk of 32 sorted points; the 8 warps of a block take
+// consecutive chunks, so their walks share node data in L1.
 template <int GF, bool COUNT>
 __global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF *__restrict__ nodes,
                                                               const int *__restrict__ n_nodes,
                                                               const PointF *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              int *status, int *work)
+                                                              int *status)
 {
-    const int lane = threadIdx.x & 31;
-    const int chunks = (n + 31) >> 5;
-    for (;;) {
-        int c = 0;
-        if (lane == 0) c = atomicAdd(work, 1);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= chunks) return;
-        walk_f32_chunk<GF, COUNT>(c, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
-    }
+    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
+    if (warp * 32 >= n) return;
+    walk_f32_chunk<GF, COUNT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
 }
 
 
@@ -279,26 +271,19 @@ __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__r
     }
 }
 
-// Persistent grid: each warp takes the next chunk of 32 points from a global
-// counter until none are left, so uneven walks (dense regions) do not leave a
-// partly filled last wave of blocks.
+// One warp per chunk of 32 sorted points; the 8 warps of a block take
+// consecutive chunks, so their walks share node data in L1.
 template <int GF, bool COUNT>
 __global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD *__restrict__ nodes,
                                                               const int *__restrict__ n_nodes,
                                                               const PointD *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              int *status, int *work)
+                                                              int *status)
 {
-    const int lane = threadIdx.x & 31;
-    const int chunks = (n + 31) >> 5;
-    for (;;) {
-        int c = 0;
-        if (lane == 0) c = atomicAdd(work, 1);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= chunks) return;
-        walk_f64_chunk<GF, COUNT>(c, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
-    }
+    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
+    if (warp * 32 >= n) return;
+    walk_f64_chunk<GF, COUNT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
 }
 
 
@@ -383,15 +368,13 @@ void launch_walk(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int warps = (n + 31) / 32;
-    const int need = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
-    const int blocks = std::max(1, std::min(need, c->sm_count * kWalkBlocksPerSM));
+    const int blocks = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
     const bool cnt = c->counters_on != 0;  // counters accumulate while enabled
-    cudaMemsetAsync(c->work, 0, sizeof(int), c->stream);
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
 #define HTS_WALK(GF, CT) \
     walk_f32_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes32, c->n_nodes, c->spts32, c->idx, \
-                                                                  c->frep, c->zi, c->counters, c->status, c->work)
+                                                                  c->frep, c->zi, c->counters, c->status)
         if (c->cfg.grad_form == HTS_EXACT_KL) {
             if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
         } else {
@@ -401,7 +384,7 @@ void launch_walk(hts_ctx *c)
     } else {
 #define HTS_WALK(GF, CT) \
     walk_f64_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes64, c->n_nodes, c->spts64, c->idx, \
-                                                                  c->frep, c->zi, c->counters, c->status, c->work)
+                                                                  c->frep, c->zi, c->counters, c->status)
         if (c->cfg.grad_form == HTS_EXACT_KL) {
             if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
         } else {
