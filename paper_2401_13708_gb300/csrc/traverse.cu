@@ -32,7 +32,6 @@ namespace hts {
 namespace {
 
 constexpr int kWalkBlock = 256;
-constexpr bool kWalkPairs = true;  // float32 walk with two queries per lane
 constexpr int kExactBlock = 256;
 
 __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int k)
@@ -163,168 +162,6 @@ __global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF
     walk_f32_chunk<GF, COUNT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
 }
 
-// ---- float32 walk with two queries per lane -------------------------------
-// A warp takes 64 consecutive sorted points; lane l holds points 2l and 2l+1
-// (neighbours in key order, so their walks almost coincide).  The two queries'
-// coordinates, accumulators and pair terms live in the two halves of float2
-// registers and use the paired float32 instructions (add / mul / fma on
-// f32x2), so node loads, votes, loop control and most arithmetic are shared by
-// two queries; only the special-function operations stay scalar.  Each query
-// keeps its own resume index, so it still accumulates exactly its own walk.
-__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
-
-template <int GF>
-__device__ __forceinline__ void pair_terms_f32x2(float2 D, float2 &W, float2 &REP)
-{
-    D = make_float2(fmaxf(D.x, 1e-30f), fmaxf(D.y, 1e-30f));
-    const float2 X = __fmul2_rn(D, __fadd2_rn(D, bc2(2.0f)));          // sinh(d)^2
-    const float2 RS = make_float2(rsqrtf(X.x), rsqrtf(X.y));            // 1 / sinh(d)
-    const float2 T = __fmul2_rn(X, RS);                                 // sinh(d)
-    float2 FS = bc2(-8.0f / 693.0f);                                    // d / sinh(d), series
-    FS = __ffma2_rn(FS, D, bc2(8.0f / 315.0f));
-    FS = __ffma2_rn(FS, D, bc2(-2.0f / 35.0f));
-    FS = __ffma2_rn(FS, D, bc2(2.0f / 15.0f));
-    FS = __ffma2_rn(FS, D, bc2(-1.0f / 3.0f));
-    FS = __ffma2_rn(FS, D, bc2(1.0f));
-    const float2 A = __fadd2_rn(__fadd2_rn(bc2(1.0f), D), T);
-    const float2 L = __fmul2_rn(make_float2(__log2f(A.x), __log2f(A.y)), bc2(0.69314718f));  // log = log2 * ln 2
-    const float2 LR = __fmul2_rn(L, RS);
-    const float2 TF = __fmul2_rn(T, FS);
-    const bool s0 = D.x < 0.1f, s1 = D.y < 0.1f;
-    const float2 F = make_float2(s0 ? FS.x : LR.x, s1 ? FS.y : LR.y);   // d / sinh(d)
-    const float2 Dd = make_float2(s0 ? TF.x : L.x, s1 ? TF.y : L.y);    // d
-    const float2 U = __ffma2_rn(Dd, Dd, bc2(1.0f));
-    W = make_float2(__fdividef(1.0f, U.x), __fdividef(1.0f, U.y));
-    const float2 ATT = __fmul2_rn(W, GF == 0 ? F : RS);
-    REP = __fmul2_rn(W, ATT);
-}
-
-template <int GF, bool COUNT>
-__device__ __forceinline__ void walk_f32x2_chunk(int warp, int n, const NodeF *__restrict__ nodes,
-                                                  const int *__restrict__ n_nodes,
-                                                  const PointF *__restrict__ spts,
-                                                  const uint32_t *__restrict__ idx, double2 *frep, double *zi,
-                                                  unsigned long long *counters)
-{
-    const int lane = threadIdx.x & 31;
-    const int p0 = warp * 64 + 2 * lane, p1 = p0 + 1;
-    const bool v0 = p0 < n, v1 = p1 < n;
-    const PointF q0 = spts[v0 ? p0 : n - 1], q1 = spts[v1 ? p1 : n - 1];
-    const float2 QXH = make_float2(q0.xh, q1.xh), QYH = make_float2(q0.yh, q1.yh);
-    const float2 QXL = make_float2(q0.xl, q1.xl), QYL = make_float2(q0.yl, q1.yl);
-    const float2 TWOIL = make_float2(2.0f * q0.il, 2.0f * q1.il);
-    float2 RX = bc2(0.f), RY = bc2(0.f), RS = bc2(0.f), Z = bc2(0.f);
-    const int m = min(*n_nodes, 2 * n);
-    int res0 = v0 ? 0 : INT_MAX, res1 = v1 ? 0 : INT_MAX;
-    int node = 0;
-    unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
-    while (node < m) {
-        const NodeF c = load_node(nodes, node);
-        const bool a0 = node >= res0, a1 = node >= res1;
-        int next = node + 1;
-        if (c.count >= 2) {
-            const float2 DX = __fadd2_rn(__fadd2_rn(QXH, bc2(-c.xh)), __fadd2_rn(QXL, bc2(-c.xl)));
-            const float2 DY = __fadd2_rn(__fadd2_rn(QYH, bc2(-c.yh)), __fadd2_rn(QYL, bc2(-c.yl)));
-            const float2 S = __ffma2_rn(DX, DX, __fmul2_rn(DY, DY));
-            const float2 D = __fmul2_rn(S, __fmul2_rn(TWOIL, bc2(c.il)));
-            const bool acc0 = a0 && D.x > c.thr, acc1 = a1 && D.y > c.thr;
-            if (acc0 || acc1) {
-                float2 W, REP;
-                pair_terms_f32x2<GF>(D, W, REP);
-                const float N = (float)c.count;
-                const float2 M = make_float2(acc0 ? N : 0.0f, acc1 ? N : 0.0f);
-                const float2 K = __fmul2_rn(__fmul2_rn(M, REP), bc2(c.il));
-                RX = __ffma2_rn(K, DX, RX);
-                RY = __ffma2_rn(K, DY, RY);
-                RS = __ffma2_rn(K, S, RS);
-                Z = __ffma2_rn(M, W, Z);
-                if (acc0) res0 = c.skip;
-                if (acc1) res1 = c.skip;
-                if (COUNT) c_acc += (unsigned)acc0 + (unsigned)acc1;
-            }
-            if (!__any_sync(0xffffffffu, (a0 && !acc0) || (a1 && !acc1))) next = c.skip;
-        } else if (c.count == 1) {
-            const int pos = __float_as_int(c.thr);
-            const bool i0 = a0 && pos != p0, i1 = a1 && pos != p1;
-            if (i0 || i1) {
-                const float2 DX = __fadd2_rn(__fadd2_rn(QXH, bc2(-c.xh)), __fadd2_rn(QXL, bc2(-c.xl)));
-                const float2 DY = __fadd2_rn(__fadd2_rn(QYH, bc2(-c.yh)), __fadd2_rn(QYL, bc2(-c.yl)));
-                const float2 S = __ffma2_rn(DX, DX, __fmul2_rn(DY, DY));
-                const float2 D = __fmul2_rn(S, __fmul2_rn(TWOIL, bc2(c.il)));
-                float2 W, REP;
-                pair_terms_f32x2<GF>(D, W, REP);
-                const float2 M = make_float2(i0 ? 1.0f : 0.0f, i1 ? 1.0f : 0.0f);
-                const float2 K = __fmul2_rn(__fmul2_rn(M, REP), bc2(c.il));
-                RX = __ffma2_rn(K, DX, RX);
-                RY = __ffma2_rn(K, DY, RY);
-                RS = __ffma2_rn(K, S, RS);
-                Z = __fadd2_rn(Z, __fmul2_rn(M, W));
-                if (COUNT) c_pair += (unsigned)i0 + (unsigned)i1;
-            }
-        } else {
-            const int lo = __float_as_int(c.thr), cnt = -c.count;
-            if ((a0 || a1) && lo >= 0 && cnt > 0 && lo + cnt <= n) {
-                for (int k2 = 0; k2 < cnt; ++k2) {
-                    const int pj = lo + k2;
-                    const bool i0 = a0 && pj != p0, i1 = a1 && pj != p1;
-                    const PointF o = spts[pj];
-                    const float2 DX = __fadd2_rn(__fadd2_rn(QXH, bc2(-o.xh)), __fadd2_rn(QXL, bc2(-o.xl)));
-                    const float2 DY = __fadd2_rn(__fadd2_rn(QYH, bc2(-o.yh)), __fadd2_rn(QYL, bc2(-o.yl)));
-                    const float2 S = __ffma2_rn(DX, DX, __fmul2_rn(DY, DY));
-                    const float2 D = __fmul2_rn(S, __fmul2_rn(TWOIL, bc2(o.il)));
-                    float2 W, REP;
-                    pair_terms_f32x2<GF>(D, W, REP);
-                    const float2 M = make_float2(i0 ? 1.0f : 0.0f, i1 ? 1.0f : 0.0f);
-                    const float2 K = __fmul2_rn(__fmul2_rn(M, REP), bc2(o.il));
-                    RX = __ffma2_rn(K, DX, RX);
-                    RY = __ffma2_rn(K, DY, RY);
-                    RS = __ffma2_rn(K, S, RS);
-                    Z = __fadd2_rn(Z, __fmul2_rn(M, W));
-                    if (COUNT) c_pair += (unsigned)i0 + (unsigned)i1;
-                }
-            }
-        }
-        if (COUNT && lane == 0) ++c_visit;
-        node = max(next, node + 1);  // always advances: the loop ends within m visits
-    }
-    auto finish = [&](int p, const PointF &q, float rx, float ry, float rs, float z) {
-        const uint32_t i = idx[p];
-        double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
-        double il = (double)q.il;
-        double rsd = il * (double)rs;
-        frep[i] = make_double2(4.0 * il * ((double)rx + rsd * x), 4.0 * il * ((double)ry + rsd * y));
-        zi[i] = (double)z;
-    };
-    if (v0) finish(p0, q0, RX.x, RY.x, RS.x, Z.x);
-    if (v1) finish(p1, q1, RX.y, RY.y, RS.y, Z.y);
-    if (COUNT) {
-        for (int o = 16; o > 0; o >>= 1) {
-            c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o);
-            c_pair += __shfl_xor_sync(0xffffffffu, c_pair, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&counters[0], c_acc);
-            atomicAdd(&counters[1], c_pair);
-            atomicAdd(&counters[2], c_visit);
-            atomicAdd(&counters[3], (unsigned long long)min(64, n - warp * 64));
-        }
-    }
-}
-
-template <int GF, bool COUNT>
-__global__ void __launch_bounds__(kWalkBlock) walk_f32x2_kernel(int n, const NodeF *__restrict__ nodes,
-                                                                const int *__restrict__ n_nodes,
-                                                                const PointF *__restrict__ spts,
-                                                                const uint32_t *__restrict__ idx, double2 *frep,
-                                                                double *zi, unsigned long long *counters)
-{
-    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
-    if (warp * 64 >= n) return;
-    walk_f32x2_chunk<GF, COUNT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters);
-}
-
-
-// One warp walks for the 32 sorted points of chunk `warp`.
 template <int GF, bool COUNT>
 __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__restrict__ nodes,
                                                 const int *__restrict__ n_nodes,
@@ -516,18 +353,7 @@ void launch_walk(hts_ctx *c)
     const int blocks = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
     const bool cnt = c->counters_on != 0;  // counters accumulate while enabled
     c->launches += 1;
-    if (c->cfg.precision == HTS_FP32_MIXED && kWalkPairs) {
-        const int blocks2 = ((n + 63) / 64 * 32 + kWalkBlock - 1) / kWalkBlock;
-#define HTS_WALK(GF, CT) \
-    walk_f32x2_kernel<GF, CT><<<blocks2, kWalkBlock, 0, c->stream>>>(n, c->nodes32, c->n_nodes, c->spts32, \
-                                                                     c->idx, c->frep, c->zi, c->counters)
-        if (c->cfg.grad_form == HTS_EXACT_KL) {
-            if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
-        } else {
-            if (cnt) HTS_WALK(1, true); else HTS_WALK(1, false);
-        }
-#undef HTS_WALK
-    } else if (c->cfg.precision == HTS_FP32_MIXED) {
+    if (c->cfg.precision == HTS_FP32_MIXED) {
 #define HTS_WALK(GF, CT) \
     walk_f32_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes32, c->n_nodes, c->spts32, c->idx, \
                                                                   c->frep, c->zi, c->counters, c->status)
