@@ -346,6 +346,12 @@ def run_ours(args, rank, world, local):
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     achieved = flops / (walk_ms * 1e-3) / 1e12
     dominant = max(prof, key=prof.get)
+    traffic = None  # DRAM bytes per walk launch from the committed ncu capture, scaled to n
+    tf = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if os.path.exists(tf):
+        rec = json.load(open(tf))
+        if rec.get("kernel") == "walk_f32_kernel" and rec.get("dram_bytes_per_launch"):
+            traffic = rec["dram_bytes_per_launch"] * n / rec["captured_n"]
 
     # ---- end to end through the C ABI, all iteration state in host memory -
     k_e2e = max(3, min(K, 20))
@@ -428,7 +434,7 @@ def run_ours(args, rank, world, local):
                                    "interactions_per_point": (acc + pairs) / max(queries, 1),
                                    "replay_reproduced_trajectory": replay_same},
         "roofline": {"kernel": "walk_f32_kernel (BH tree walk)", "bound": "alu", "achieved": achieved,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "dominant_phase": dominant, "walk_ms": walk_ms,
                      "peak_basis": "FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (sampled SM clock)" % (
                          props.multi_processor_count, sm_mhz)},
