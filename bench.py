@@ -347,7 +347,7 @@ def run_ours(args, rank, world, local):
     achieved = flops / (walk_ms * 1e-3) / 1e12
     dominant = max(prof, key=prof.get)
     traffic = None  # DRAM bytes per walk launch from the committed ncu capture, scaled to n
-    tf = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    tf = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     if os.path.exists(tf):
         rec = json.load(open(tf))
         if rec.get("kernel") == "walk_f32_kernel" and rec.get("dram_bytes_per_launch"):
