@@ -195,10 +195,13 @@ struct PairF {
 // from d = log(1 + delta + sinh d) with the hardware log2, whose absolute
 // error (~2^-22) is small against d >= 0.44 there.  Relative error of every
 // returned term stays below ~1e-6.
+// delta is held in [1e-30, 1e18]: the top keeps delta (delta + 2) finite in
+// float32 for points within 1e-9 of the rim (there d ~ 42 and the pair's
+// force is ~1e-3 of a unit-distance pair's).
 template <int GF>
 __device__ __forceinline__ PairF pair_terms_f32(float delta)
 {
-    delta = fmaxf(delta, 1e-30f);
+    delta = fminf(fmaxf(delta, 1e-30f), 1e18f);
     const float x = delta * (delta + 2.0f);  // sinh(d)^2
     const float rs = rsqrtf(x);              // 1 / sinh(d)
     const float t = x * rs;                  // sinh(d)
