@@ -72,15 +72,12 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
         const NodeF c = load_node(nodes, node);
         const bool active = node >= resume;
         int next = node + 1;
-        if (c.count >= 1) {
-            // internal cell (count >= 2) or single-point leaf (count == 1): one
-            // code path; a leaf is accepted by every active lane but its own
-            const bool leaf = c.count == 1;
+        if (c.count >= 2) {
             float dx = (q.xh - c.xh) + (q.xl - c.xl);
             float dy = (q.yh - c.yh) + (q.yl - c.yl);
             float s = fmaf(dx, dx, dy * dy);
             float delta = s * twoil * c.il;
-            bool acc = active && (leaf ? __float_as_int(c.thr) != p : delta > c.thr);
+            bool acc = active && delta > c.thr;
             if (acc) {
                 PairF t = pair_terms_f32<GF>(delta);
                 float mult = (float)c.count;
@@ -90,11 +87,22 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
                 rs = fmaf(k, s, rs);
                 z = fmaf(mult, t.w, z);
                 resume = c.skip;
-                if (COUNT) {
-                    if (leaf) ++c_pair; else ++c_acc;
-                }
+                if (COUNT) ++c_acc;
             }
-            if (!leaf && !__any_sync(0xffffffffu, active && !acc)) next = c.skip;
+            if (!__any_sync(0xffffffffu, active && !acc)) next = c.skip;
+        } else if (c.count == 1) {
+            if (active && __float_as_int(c.thr) != p) {
+                float dx = (q.xh - c.xh) + (q.xl - c.xl);
+                float dy = (q.yh - c.yh) + (q.yl - c.yl);
+                float s = fmaf(dx, dx, dy * dy);
+                PairF t = pair_terms_f32<GF>(s * twoil * c.il);
+                float k = t.rep * c.il;
+                rx = fmaf(k, dx, rx);
+                ry = fmaf(k, dy, ry);
+                rs = fmaf(k, s, rs);
+                z += t.w;
+                if (COUNT) ++c_pair;
+            }
         } else {
             const int lo = __float_as_int(c.thr), cnt = -c.count;
             if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
