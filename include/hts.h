@@ -213,6 +213,61 @@ HTS_API int hts_set_state(hts_ctx *ctx, const double *vel, const double *gains, 
  * (negative or non-finite |x|^2), HTS_EOOM, HTS_ECUDA. */
 HTS_API int hts_set_cosne(hts_ctx *ctx, double lambda1, double lambda2, const double *x_sqnorm, int where);
 
+/* ---- batched embeddings ---------------------------------------------------
+ * Up to HTS_MAX_SEGMENTS independent embeddings (different data sets,
+ * perplexities or seeds) share one context: the n points are split into
+ * nseg consecutive ranges [offsets[s], offsets[s+1]) (host int64[nseg+1],
+ * offsets[0] = 0, offsets[nseg] = n, every range non-empty), and P must be
+ * block diagonal (each row indexes only points of its own segment; checked
+ * on the device).  Every segment gets its own root annulus and polar
+ * quadtree (Sec. 4.1; the segment id is the top 6 key bits, so the trees form
+ * one forest built by the same launches), its own Z, and its own learning
+ * rate lr * lr_scale[s] in hts_step (lr_scale: host double[nseg], NULL = all
+ * 1; the paper's lr = n_s / 12000 is lr = 1/12000 with lr_scale[s] = n_s).
+ * All segments advance in the same kernel launches.  nseg = 1 restores the
+ * single-embedding behaviour (lr_scale is then ignored); hts_set_Y with
+ * another n resets to nseg = 1, and so does hts_set_P with another n.  With
+ * segments, the CO-SNE term of hts_set_cosne uses the segment's size n_s in
+ * place of n.
+ * Errors (each leaves the context with nseg = 1): HTS_ENOTSET (set P and Y
+ * first), HTS_EINVAL, HTS_ESHAPE (bad offsets or P not block diagonal),
+ * HTS_EOOM, HTS_ECUDA. */
+#define HTS_MAX_SEGMENTS 64
+HTS_API int hts_set_segments(hts_ctx *ctx, int nseg, const int64_t *offsets, const double *lr_scale);
+
+/* Per-segment Z of the last hts_grad / hts_step / hts_kl (host double[nseg]). */
+HTS_API int hts_get_segment_Z(hts_ctx *ctx, double *Z_out);
+
+/* Per-segment KL (host double[nseg]), Z from the tree (theta > 0) or exact
+ * (theta == 0) within each segment.  hts_kl returns their sum. */
+HTS_API int hts_kl_segments(hts_ctx *ctx, double theta, double *kl_out);
+
+/* Replay each hts_step iteration as one CUDA graph (captured on a private
+ * stream ordered after the context's stream by events; re-captured when
+ * theta, exaggeration, lr, momentum or the problem changes).  Saves launch
+ * overhead at small n; results are identical.  Off by default. */
+HTS_API int hts_set_graphs(hts_ctx *ctx, int enable);
+
+/* ---- launch-shape autotuner ------------------------------------------------
+ * (No counterpart in the paper, whose implementation is a CPU program.)  Two
+ * launch shapes of the hot path depend on the problem: the BH walk's threads
+ * per block (32, 64, 128 or 256; each warp walks 32 key-adjacent points, and
+ * small blocks spread a small problem over more SMs) and the float32
+ * attraction's lanes per row of P (4, 8, 16 or 32; matched to the row
+ * lengths).  hts_autotune builds the tree for the current Y once (theta > 0),
+ * times `reps` launches of every candidate of each kernel on the context's
+ * stream with CUDA events, keeps the fastest and writes the choice to
+ * tuning[2] = {walk threads per block, attraction lanes per row} (may be
+ * NULL).  It changes no result of the walk (the work split per warp does not
+ * depend on the block size); lanes per row change only the float32 summation
+ * order inside a row.  hts_set_tuning sets them directly (0 keeps a value),
+ * hts_get_tuning reads them.  Defaults: {256, 8}.  Errors: HTS_ENOTSET,
+ * HTS_EINVAL (theta outside [0, 1], reps outside [1, 1000], a value not in
+ * the lists), HTS_ECUDA. */
+HTS_API int hts_autotune(hts_ctx *ctx, double theta, int reps, int *tuning);
+HTS_API int hts_set_tuning(hts_ctx *ctx, int walk_block, int attract_lanes);
+HTS_API int hts_get_tuning(const hts_ctx *ctx, int *tuning);
+
 /* Number of points n and non-zeros nnz currently set (either may be NULL). */
 HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);
 

@@ -36,8 +36,10 @@ EXPORTS = [
     "hts_default_config", "hts_create", "hts_destroy", "hts_set_P", "hts_set_Y", "hts_step", "hts_get_Y",
     "hts_grad", "hts_kl", "hts_last_error", "hts_get_keys", "hts_get_tree", "hts_get_counters",
     "hts_set_counters", "hts_get_state", "hts_set_state", "hts_get_sizes", "hts_set_profiling",
-    "hts_get_profile", "hts_exact_grad_noalloc", "hts_set_cosne",
+    "hts_get_profile", "hts_exact_grad_noalloc", "hts_set_cosne", "hts_set_segments", "hts_get_segment_Z",
+    "hts_kl_segments", "hts_set_graphs", "hts_autotune", "hts_set_tuning", "hts_get_tuning",
 ]
+MAX_SEGMENTS = 64
 
 
 class HtsConfig(C.Structure):
@@ -97,6 +99,13 @@ def load(path: str = LIB_PATH):
             "hts_get_profile": (i32, [vp, vp, vp]),
             "hts_exact_grad_noalloc": (i32, [i64, i64, vp, vp, vp, vp, d, i32, vp, vp, vp]),
             "hts_set_cosne": (i32, [vp, d, d, vp, i32]),
+            "hts_set_segments": (i32, [vp, i32, vp, vp]),
+            "hts_get_segment_Z": (i32, [vp, vp]),
+            "hts_kl_segments": (i32, [vp, d, vp]),
+            "hts_set_graphs": (i32, [vp, i32]),
+            "hts_autotune": (i32, [vp, d, i32, vp]),
+            "hts_set_tuning": (i32, [vp, i32, i32]),
+            "hts_get_tuning": (i32, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -110,6 +110,8 @@ class HyperbolicTSNE:
         if len({w0, w1, w2}) != 1:
             raise ValueError("indptr, indices and values must all be host or all device")
         self._check(self._lib.hts_set_P(self._ctx, n, nnz, p0, p1, p2, F64 if vdt is np.float64 else F32, w0))
+        if n != getattr(self, "n", n):
+            self.nseg = 1
         del k0, k1, k2
 
     def set_Y(self, y):
@@ -117,6 +119,8 @@ class HyperbolicTSNE:
         n = int(y.shape[0])
         p, w, keep = _arg(y, np.float64)
         self._check(self._lib.hts_set_Y(self._ctx, n, p, w))
+        if n != getattr(self, "n", n):
+            self.nseg = 1  # the library drops segments when n changes
         self.n = n
         del keep
 
@@ -155,6 +159,51 @@ class HyperbolicTSNE:
         v = C.c_double(0.0)
         self._check(self._lib.hts_kl(self._ctx, float(theta), C.byref(v)))
         return v.value
+
+    # -- batched embeddings ---------------------------------------------------
+    def set_segments(self, offsets, lr_scale=None):
+        """Split the n points into independent embeddings [offsets[s], offsets[s+1])."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        nseg = off.size - 1
+        self.nseg = max(nseg, 1)
+        lr = None if lr_scale is None else np.ascontiguousarray(lr_scale, dtype=np.float64)
+        if lr is not None and lr.size != nseg:
+            raise ValueError("lr_scale needs one value per segment")
+        code = self._lib.hts_set_segments(self._ctx, int(nseg), off.ctypes.data_as(C.c_void_p),
+                                          None if lr is None else lr.ctypes.data_as(C.c_void_p))
+        if code != 0:
+            self.nseg = 1  # an error leaves one segment
+        self._check(code)
+
+    def segment_Z(self):
+        z = np.zeros(getattr(self, "nseg", 1))
+        self._check(self._lib.hts_get_segment_Z(self._ctx, z.ctypes.data_as(C.c_void_p)))
+        return z
+
+    def kl_segments(self, theta: float):
+        v = np.zeros(getattr(self, "nseg", 1))
+        self._check(self._lib.hts_kl_segments(self._ctx, float(theta), v.ctypes.data_as(C.c_void_p)))
+        return v
+
+    # -- launch shapes --------------------------------------------------------
+    def autotune(self, theta: float = 0.5, reps: int = 5):
+        """Time the launch-shape candidates on the current problem; returns
+        (walk threads per block, attraction lanes per row)."""
+        out = (C.c_int * 2)()
+        self._check(self._lib.hts_autotune(self._ctx, float(theta), int(reps), out))
+        return int(out[0]), int(out[1])
+
+    def set_tuning(self, walk_block: int = 0, attract_lanes: int = 0):
+        self._check(self._lib.hts_set_tuning(self._ctx, int(walk_block), int(attract_lanes)))
+
+    def get_tuning(self):
+        out = (C.c_int * 2)()
+        self._check(self._lib.hts_get_tuning(self._ctx, out))
+        return int(out[0]), int(out[1])
+
+    def set_graphs(self, enable: bool = True):
+        """Replay each step iteration as one CUDA graph (same results, fewer launches)."""
+        self._check(self._lib.hts_set_graphs(self._ctx, 1 if enable else 0))
 
     # -- inspection -----------------------------------------------------------
     def get_keys(self):

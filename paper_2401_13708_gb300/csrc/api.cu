@@ -233,6 +233,106 @@ int check_theta(hts_ctx *c, double theta)
     return HTS_OK;
 }
 
+void free_segments(hts_ctx *c)
+{
+    dfree(&c->seg_off);
+    dfree(&c->seg_of);
+    dfree(&c->seg_lr);
+    dfree(&c->seg_z);
+    c->nseg = 1;
+    c->seg_off_h[0] = 0;
+    c->seg_off_h[1] = c->n;
+}
+
+void drop_graph(hts_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey[0] = -1.0;
+}
+
+// Capture one iteration (gradient + update) into c->gexec on the private
+// stream, unless the cached graph already matches the arguments and layout.
+int capture_iteration(hts_ctx *c, double theta, double exag, double lr, double mom)
+{
+    const double key[5] = {theta, exag, lr, mom, (double)c->layout_version};
+    if (c->gexec && memcmp(key, c->gkey, sizeof(key)) == 0) return HTS_OK;
+    drop_graph(c);
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming));
+    }
+    cudaStream_t keep = c->stream;
+    const int64_t l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->gstream;
+    int r = run_gradient(c, theta);
+    if (!r) {
+        launch_update(c, exag, lr, mom, nullptr, 1);
+        r = cudaGetLastError() == cudaSuccess ? HTS_OK : HTS_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+    c->stream = keep;
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    if (r || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return r ? r : cuda_fail(c, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    memcpy(c->gkey, key, sizeof(key));
+    return HTS_OK;
+}
+
+// Per-segment KL parts after run_gradient (Z only): kl[s] for s < nseg.
+int kl_parts(hts_ctx *c, std::vector<double> &kl)
+{
+    const int ns = c->nseg;
+    std::vector<double> h(4 * (size_t)ns, 0.0);  // Z, sum p log p, sum p log w, sum p
+    const double *zsrc = ns > 1 ? c->seg_z : c->dscal;
+    CK(cudaMemcpyAsync(h.data(), zsrc, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->stream));
+    if (c->nnz > 0 && ns == 1) {
+        launch_kl_terms(c);
+        LAUNCHED("kl_terms");
+        CK(cudaMemcpyAsync(h.data() + 1, c->dscal + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    } else if (c->nnz > 0) {
+        const size_t n = (size_t)c->n;
+        double *a = c->terms, *b = c->terms + n, *pp = c->terms + 2 * n;  // 3n doubles of scratch
+        launch_kl_rows(c, a, b, pp);
+        LAUNCHED("kl_rows");
+        double *out = c->red_tmp;  // >= 3 * HTS_MAX_SEGMENTS doubles
+        launch_segment_sums(c, a, out);
+        launch_segment_sums(c, b, out + HTS_MAX_SEGMENTS);
+        launch_segment_sums(c, pp, out + 2 * HTS_MAX_SEGMENTS);
+        LAUNCHED("segment_sums");
+        for (int k = 0; k < 3; ++k)
+            CK(cudaMemcpyAsync(h.data() + (size_t)(k + 1) * ns, out + k * HTS_MAX_SEGMENTS, sizeof(double) * ns,
+                               cudaMemcpyDeviceToHost, c->stream));
+    }
+    int st = 0;
+    int r = read_status(c, &st);  // synchronises the stream
+    if (r) return r;
+    if ((r = status_error(c, st))) return r;
+    kl.assign((size_t)ns, 0.0);
+    for (int s = 0; s < ns; ++s) {
+        double Z, a, b, sp;
+        if (ns == 1) {
+            Z = h[0]; a = h[1]; b = h[2]; sp = h[3];
+        } else {
+            Z = h[s]; a = h[(size_t)ns + s]; b = h[2 * (size_t)ns + s]; sp = h[3 * (size_t)ns + s];
+        }
+        kl[s] = a - b + (sp > 0.0 ? sp * log(Z) : 0.0);
+    }
+    return HTS_OK;
+}
+
 __global__ void convert_values_kernel(int64_t nnz, const void *in, int in_f64, void *out, int out_f64)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,7 +392,7 @@ int hts_create(hts_ctx **out, const hts_config *cfg)
         return HTS_ECUDA;
     }
     c->sm_count = prop.multiProcessorCount;
-    if (dalloc(c, &c->minmax, 2) || dalloc(c, &c->dscal, 8) || dalloc(c, &c->status, 1) ||
+    if (dalloc(c, &c->minmax, 2 * kMaxSegments) || dalloc(c, &c->dscal, 8) || dalloc(c, &c->status, 1) ||
         dalloc(c, &c->counters, 4) || cudaMallocHost((void **)&c->h_pinned, 8 * sizeof(double)) != cudaSuccess) {
         hts_destroy(c);
         return HTS_EOOM;
@@ -318,6 +418,14 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
     dfree(&c->sort_counts); dfree(&c->scan_tmp); dfree(&c->red_tmp); dfree(&c->minmax);
     dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq);
+    dfree(&c->seg_off); dfree(&c->seg_of); dfree(&c->seg_lr); dfree(&c->seg_z);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gstream) {
+        cudaStreamSynchronize(c->gstream);
+        cudaStreamDestroy(c->gstream);
+    }
+    if (c->gev_in) cudaEventDestroy(c->gev_in);
+    if (c->gev_out) cudaEventDestroy(c->gev_out);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     for (int k = 0; k < c->event_slots * (kPhases + 1); ++k) cudaEventDestroy(c->events[k]);
     delete[] c->events;
@@ -407,8 +515,23 @@ int hts_set_P(hts_ctx *c, int64_t n, int64_t nnz, const int64_t *indptr, const i
     }
     CK(cudaStreamSynchronize(c->stream));
     c->values_f64 = out_f64;
-    c->n = n;
     c->nnz = nnz;
+    c->layout_version += 1;
+    if (c->nseg > 1 && n == c->n && n > 0) {  // segments stay: P must respect them
+        CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        launch_segments_setup(c);
+        LAUNCHED("segments_setup");
+        int st = 0;
+        if ((r = read_status(c, &st))) return r;
+        if (st) {
+            c->have_P = false;
+            return fail(c, HTS_ESHAPE, "hts_set_P: P is not block diagonal over the segments");
+        }
+    } else if (c->nseg > 1) {
+        free_segments(c);
+    }
+    c->n = n;
+    c->seg_off_h[1] = c->nseg == 1 ? n : c->seg_off_h[1];
     c->have_P = true;
     return HTS_OK;
 }
@@ -436,6 +559,9 @@ int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
         c->cosne_l1 = 1.0;
         c->cosne_l2 = 0.0;
     }
+    if (n != c->n && c->nseg > 1) free_segments(c);
+    // buffers move (and captured graphs go stale) only when the size changes
+    if (n != c->n || n != c->cap_n || !(c->pts32 || c->pts64)) c->layout_version += 1;
     if ((r = ensure_points(c, n))) return r;
     if (n > 0) {
         CK(cudaMemcpyAsync(c->y, y, sizeof(double2) * (size_t)n,
@@ -456,6 +582,7 @@ int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
         }
     }
     c->n = n;
+    if (c->nseg == 1) c->seg_off_h[1] = n;
     c->iters = 0;
     c->have_Y = true;
     return HTS_OK;
@@ -473,12 +600,22 @@ int hts_step(hts_ctx *c, int n_iter, double theta, double exaggeration, double l
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     const int prof = c->profiling ? std::min(n_iter, 4096) : 0;
     if (prof && (r = ensure_events(c, prof))) return r;
-    for (int it = 0; it < n_iter; ++it) {
-        cudaEvent_t *ev = it < prof ? c->events + (size_t)it * (kPhases + 1) : nullptr;
-        if ((r = run_gradient(c, theta, ev))) return r;
-        launch_update(c, exaggeration, lr, momentum, nullptr, 1);
-        LAUNCHED("update");
-        if (ev) CK(cudaEventRecord(ev[kPhases], c->stream));
+    if (c->use_graphs && !prof && !c->counters_on) {
+        if ((r = capture_iteration(c, theta, exaggeration, lr, momentum))) return r;
+        CK(cudaEventRecord(c->gev_in, c->stream));
+        CK(cudaStreamWaitEvent(c->gstream, c->gev_in, 0));
+        for (int it = 0; it < n_iter; ++it) CK(cudaGraphLaunch(c->gexec, c->gstream));
+        CK(cudaEventRecord(c->gev_out, c->gstream));
+        CK(cudaStreamWaitEvent(c->stream, c->gev_out, 0));
+        c->launches += c->graph_launches * n_iter;
+    } else {
+        for (int it = 0; it < n_iter; ++it) {
+            cudaEvent_t *ev = it < prof ? c->events + (size_t)it * (kPhases + 1) : nullptr;
+            if ((r = run_gradient(c, theta, ev))) return r;
+            launch_update(c, exaggeration, lr, momentum, nullptr, 1);
+            LAUNCHED("update");
+            if (ev) CK(cudaEventRecord(ev[kPhases], c->stream));
+        }
     }
     c->iters += n_iter;
     int st = 0;
@@ -554,18 +691,11 @@ int hts_kl(hts_ctx *c, double theta, double *kl_out)
     r = run_gradient(c, theta);
     c->nnz = keep;
     if (r) return r;
-    if (c->nnz > 0) {
-        launch_kl_terms(c);
-        LAUNCHED("kl_terms");
-    } else {
-        CK(cudaMemsetAsync(c->dscal + 1, 0, 3 * sizeof(double), c->stream));
-    }
-    CK(cudaMemcpyAsync(c->h_pinned + 2, c->dscal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    int st = 0;
-    if ((r = read_status(c, &st))) return r;
-    if ((r = status_error(c, st))) return r;
-    double Z = c->h_pinned[2], plogp = c->h_pinned[3], plogw = c->h_pinned[4], sp = c->h_pinned[5];
-    *kl_out = plogp - plogw + (sp > 0.0 ? sp * log(Z) : 0.0);
+    std::vector<double> kl;
+    if ((r = kl_parts(c, kl))) return r;
+    double t = 0.0;
+    for (double v : kl) t += v;
+    *kl_out = t;
     return HTS_OK;
 }
 
@@ -662,6 +792,7 @@ int hts_set_counters(hts_ctx *c, int enable)
     if (r) return r;
     if (enable && !c->counters_on) CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream));
     c->counters_on = enable ? 1 : 0;
+    c->layout_version += 1;
     return HTS_OK;
 }
 
@@ -733,6 +864,7 @@ int hts_set_cosne(hts_ctx *c, double lambda1, double lambda2, const double *x_sq
         dfree(&c->xsq);
         c->cosne_l1 = 1.0;
         c->cosne_l2 = 0.0;
+        c->layout_version += 1;
         return HTS_OK;
     }
     if (!c->have_Y) return fail(c, HTS_ENOTSET, "hts_set_cosne: set Y first (the term is per point)");
@@ -754,6 +886,193 @@ int hts_set_cosne(hts_ctx *c, double lambda1, double lambda2, const double *x_sq
     CK(cudaStreamSynchronize(c->stream));
     c->cosne_l1 = lambda1;
     c->cosne_l2 = lambda2;
+    c->layout_version += 1;
+    return HTS_OK;
+}
+
+int hts_set_segments(hts_ctx *c, int nseg, const int64_t *offsets, const double *lr_scale)
+{
+    if (!c) return HTS_EINVAL;
+    c->err.clear();
+    int r = set_device(c);
+    if (r) return r;
+    CK(cudaStreamSynchronize(c->stream));
+    free_segments(c);  // every error below leaves one segment
+    c->layout_version += 1;
+    if (!c->have_P || !c->have_Y) return fail(c, HTS_ENOTSET, "hts_set_segments: set P and Y first");
+    if (nseg < 1 || nseg > HTS_MAX_SEGMENTS || !offsets) return fail(c, HTS_EINVAL, "hts_set_segments: bad nseg");
+    if (offsets[0] != 0 || offsets[nseg] != c->n)
+        return fail(c, HTS_ESHAPE, "hts_set_segments: offsets must start at 0 and end at n");
+    for (int s = 0; s < nseg; ++s)
+        if (offsets[s + 1] <= offsets[s]) return fail(c, HTS_ESHAPE, "hts_set_segments: empty or decreasing range");
+    if (lr_scale)
+        for (int s = 0; s < nseg; ++s)
+            if (!(lr_scale[s] >= 0.0) || !isfinite(lr_scale[s]))
+                return fail(c, HTS_EINVAL, "hts_set_segments: lr_scale must be finite and >= 0");
+    if (nseg == 1) return HTS_OK;
+    if ((r = dalloc(c, &c->seg_off, HTS_MAX_SEGMENTS + 1)) || (r = dalloc(c, &c->seg_of, (size_t)c->n)) ||
+        (r = dalloc(c, &c->seg_lr, HTS_MAX_SEGMENTS)) || (r = dalloc(c, &c->seg_z, HTS_MAX_SEGMENTS))) {
+        free_segments(c);
+        return r;
+    }
+    std::vector<double> lr((size_t)nseg, 1.0);
+    if (lr_scale) lr.assign(lr_scale, lr_scale + nseg);
+    cudaError_t e = cudaMemcpy(c->seg_off, offsets, sizeof(int64_t) * (size_t)(nseg + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->seg_lr, lr.data(), sizeof(double) * (size_t)nseg, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) {
+        free_segments(c);
+        return cuda_fail(c, e, "hts_set_segments: copy");
+    }
+    c->nseg = nseg;
+    launch_segments_setup(c);
+    int st = 0;
+    e = cudaGetLastError();
+    if (e != cudaSuccess || (r = read_status(c, &st)) || st) {
+        free_segments(c);
+        if (e != cudaSuccess) return cuda_fail(c, e, "segments_setup");
+        return r ? r : fail(c, HTS_ESHAPE, "hts_set_segments: P is not block diagonal over the segments");
+    }
+    for (int s = 0; s <= nseg; ++s) c->seg_off_h[s] = offsets[s];
+    return HTS_OK;
+}
+
+int hts_get_segment_Z(hts_ctx *c, double *Z_out)
+{
+    if (!c || !Z_out) return HTS_EINVAL;
+    int r = set_device(c);
+    if (r) return r;
+    CK(cudaMemcpyAsync(c->h_pinned, c->nseg > 1 ? c->seg_z : c->dscal, sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    if (c->nseg > 1)
+        CK(cudaMemcpyAsync(Z_out, c->seg_z, sizeof(double) * (size_t)c->nseg, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->nseg == 1) Z_out[0] = c->h_pinned[0];
+    return HTS_OK;
+}
+
+int hts_kl_segments(hts_ctx *c, double theta, double *kl_out)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!kl_out) return fail(c, HTS_EINVAL, "hts_kl_segments: NULL output");
+    if ((r = check_theta(c, theta))) return r;
+    if (c->n == 0) {
+        kl_out[0] = 0.0;
+        return HTS_OK;
+    }
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    int64_t keep = c->nnz;
+    c->nnz = 0;
+    r = run_gradient(c, theta);
+    c->nnz = keep;
+    if (r) return r;
+    std::vector<double> kl;
+    if ((r = kl_parts(c, kl))) return r;
+    for (int s = 0; s < c->nseg; ++s) kl_out[s] = kl[s];
+    return HTS_OK;
+}
+
+int hts_set_graphs(hts_ctx *c, int enable)
+{
+    if (!c) return HTS_EINVAL;
+    int r = set_device(c);
+    if (r) return r;
+    c->use_graphs = enable ? 1 : 0;
+    if (!enable) {
+        if (c->gstream) CK(cudaStreamSynchronize(c->gstream));
+        drop_graph(c);
+    }
+    return HTS_OK;
+}
+
+int hts_autotune(hts_ctx *c, double theta, int reps, int *tuning)
+{
+    int r = ready(c);
+    if (r) return r;
+    if ((r = check_theta(c, theta))) return r;
+    if (reps < 1 || reps > 1000) return fail(c, HTS_EINVAL, "hts_autotune: reps must be in [1, 1000]");
+    if (c->n > 0) {
+        CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        if ((r = ensure_events(c, 1))) return r;
+        cudaEvent_t a = c->events[0], b = c->events[1];
+        launch_prep_points(c);
+        LAUNCHED("prep_points");
+        auto time_it = [&](auto launch, float *ms) -> int {
+            launch();  // warm
+            CK(cudaEventRecord(a, c->stream));
+            for (int k = 0; k < reps; ++k) launch();
+            CK(cudaEventRecord(b, c->stream));
+            CK(cudaEventSynchronize(b));
+            LAUNCHED("autotune");
+            CK(cudaEventElapsedTime(ms, a, b));
+            return HTS_OK;
+        };
+        if (theta > 0.0) {
+            launch_make_keys(c);
+            launch_sort_pairs(c);
+            launch_build_tree(c, theta, nullptr);
+            LAUNCHED("build_tree");
+            const int cand[4] = {32, 64, 128, 256};
+            float best = INFINITY;
+            int pick = c->walk_block;
+            for (int wb : cand) {
+                c->walk_block = wb;
+                float ms = 0.f;
+                if ((r = time_it([&] { launch_walk(c); }, &ms))) return r;
+                if (ms < best) {
+                    best = ms;
+                    pick = wb;
+                }
+            }
+            c->walk_block = pick;
+        }
+        if (c->nnz > 0 && c->cfg.precision == HTS_FP32_MIXED) {
+            const int cand[4] = {4, 8, 16, 32};
+            float best = INFINITY;
+            int pick = c->attract_group;
+            for (int g : cand) {
+                c->attract_group = g;
+                float ms = 0.f;
+                if ((r = time_it([&] { launch_attract(c); }, &ms))) return r;
+                if (ms < best) {
+                    best = ms;
+                    pick = g;
+                }
+            }
+            c->attract_group = pick;
+        }
+        int st = 0;
+        if ((r = read_status(c, &st))) return r;
+        if ((r = status_error(c, st))) return r;
+        c->layout_version += 1;
+    }
+    if (tuning) {
+        tuning[0] = c->walk_block;
+        tuning[1] = c->attract_group;
+    }
+    return HTS_OK;
+}
+
+int hts_set_tuning(hts_ctx *c, int walk_block, int attract_lanes)
+{
+    if (!c) return HTS_EINVAL;
+    c->err.clear();
+    auto in = [](int v, int a, int b, int d, int e) { return v == a || v == b || v == d || v == e; };
+    if ((walk_block && !in(walk_block, 32, 64, 128, 256)) || (attract_lanes && !in(attract_lanes, 4, 8, 16, 32)))
+        return fail(c, HTS_EINVAL, "hts_set_tuning: walk_block in {32,64,128,256}, attract_lanes in {4,8,16,32}");
+    if (walk_block) c->walk_block = walk_block;
+    if (attract_lanes) c->attract_group = attract_lanes;
+    c->layout_version += 1;
+    return HTS_OK;
+}
+
+int hts_get_tuning(const hts_ctx *c, int *tuning)
+{
+    if (!c || !tuning) return HTS_EINVAL;
+    tuning[0] = c->walk_block;
+    tuning[1] = c->attract_group;
     return HTS_OK;
 }
 

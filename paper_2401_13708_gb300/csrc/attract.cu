@@ -16,13 +16,13 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// Float32 path: a group of kGroup lanes per row (kBlock / kGroup rows per
-// block), so short rows do not leave most of a warp idle; each lane keeps
-// kUnroll index loads and gathers in flight before its arithmetic.
-constexpr int kGroup = 8;
+// Float32 path: a group of G lanes per row (kBlock / G rows per block; G in
+// {4, 8, 16, 32}, picked by the autotuner, default 8), so short rows do not
+// leave most of a warp idle; each lane keeps kUnroll index loads and gathers
+// in flight before its arithmetic.
 constexpr int kUnroll = 4;
 
-template <int GF>
+template <int GF, int kGroup>
 __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_t *__restrict__ indptr,
                                                              const int32_t *__restrict__ indices,
                                                              const float *__restrict__ vals,
@@ -157,6 +157,69 @@ __global__ void __launch_bounds__(kBlock) kl_terms_kernel(int n, const int64_t *
     }
 }
 
+// Per-row KL terms (for per-segment sums): a[i] = sum p log p, b[i] = sum p log w,
+// pp[i] = sum p over row i, all in float64 from the float64 positions.
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) kl_rows_kernel(int n, const int64_t *__restrict__ indptr,
+                                                         const int32_t *__restrict__ indices,
+                                                         const VT *__restrict__ vals, const double2 *__restrict__ y,
+                                                         double *a_out, double *b_out, double *p_out)
+{
+    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double a = 0, b = 0, sp = 0;
+    const double2 q = y[row];
+    const double ai = 1.0 - (q.x * q.x + q.y * q.y);
+    for (int64_t e = indptr[row] + lane; e < indptr[row + 1]; e += 32) {
+        const double pv = (double)vals[e];
+        if (!(pv > 0.0)) continue;
+        const double2 o = y[indices[e]];
+        double dx = q.x - o.x, dy = q.y - o.y;
+        double bj = 1.0 - (o.x * o.x + o.y * o.y);
+        double delta = 2.0 * (dx * dx + dy * dy) / (ai * bj);
+        double d = log1p(delta + sqrt(delta * (delta + 2.0)));
+        a += pv * log(pv);
+        b -= pv * log1p(d * d);
+        sp += pv;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    }
+    if (lane == 0) {
+        a_out[row] = a;
+        b_out[row] = b;
+        p_out[row] = sp;
+    }
+}
+
+// Rows of segment s may only index points of segment s (status bit 16).
+__global__ void check_block_diagonal_kernel(int n, const int64_t *__restrict__ indptr,
+                                            const int32_t *__restrict__ indices,
+                                            const unsigned char *__restrict__ seg_of, int *status)
+{
+    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int s = seg_of[row];
+    for (int64_t e = indptr[row] + lane; e < indptr[row + 1]; e += 32)
+        if (seg_of[indices[e]] != s) atomicOr(status, 16);
+}
+
+__global__ void fill_segments_kernel(int n, int nseg, const int64_t *__restrict__ off, unsigned char *seg_of)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nseg - 1;  // last s with off[s] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    seg_of[i] = (unsigned char)lo;
+}
+
 __global__ void sum_partials_kernel(int blocks, const double *__restrict__ partial, double *out3)
 {
     __shared__ double sh[3][256];
@@ -206,16 +269,28 @@ void launch_attract(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
-    const int blocks32 = (int)(((int64_t)n * kGroup + kBlock - 1) / kBlock);
+    const int G = c->attract_group;
+    const int blocks32 = (int)(((int64_t)n * G + kBlock - 1) / kBlock);
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
         const float *v = (const float *)c->values;
-        if (c->cfg.grad_form == HTS_EXACT_KL)
-            attract_f32_kernel<0><<<blocks32, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32,
-                                                                      c->fattr);
-        else
-            attract_f32_kernel<1><<<blocks32, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32,
-                                                                      c->fattr);
+#define HTS_ATTRACT(GF, GG)                                                                             \
+    attract_f32_kernel<GF, GG><<<blocks32, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32, \
+                                                                    c->fattr)
+#define HTS_ATTRACT_G(GF)                          \
+    switch (G) {                                   \
+    case 4: HTS_ATTRACT(GF, 4); break;             \
+    case 16: HTS_ATTRACT(GF, 16); break;           \
+    case 32: HTS_ATTRACT(GF, 32); break;           \
+    default: HTS_ATTRACT(GF, 8); break;            \
+    }
+        if (c->cfg.grad_form == HTS_EXACT_KL) {
+            HTS_ATTRACT_G(0)
+        } else {
+            HTS_ATTRACT_G(1)
+        }
+#undef HTS_ATTRACT_G
+#undef HTS_ATTRACT
     } else {
         const double *v = (const double *)c->values;
         if (c->cfg.grad_form == HTS_EXACT_KL)
@@ -237,6 +312,27 @@ void launch_kl_terms(hts_ctx *c)
                                                                  c->y, c->red_tmp);
     sum_partials_kernel<<<1, 256, 0, c->stream>>>(blocks, c->red_tmp, c->dscal + 1);
     c->launches += 2;
+}
+
+void launch_kl_rows(hts_ctx *c, double *a, double *b, double *p)
+{
+    const int n = (int)c->n;
+    const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
+    if (c->values_f64)
+        kl_rows_kernel<double><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, (const double *)c->values,
+                                                                 c->y, a, b, p);
+    else
+        kl_rows_kernel<float><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, (const float *)c->values,
+                                                                c->y, a, b, p);
+    c->launches += 1;
+}
+
+void launch_segments_setup(hts_ctx *c)
+{
+    const int n = (int)c->n;
+    fill_segments_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->nseg, c->seg_off, c->seg_of);
+    const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
+    check_block_diagonal_kernel<<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, c->seg_of, c->status);
 }
 
 void launch_validate_csr(hts_ctx *c, int n, int64_t nnz, const int64_t *indptr, const int32_t *indices,

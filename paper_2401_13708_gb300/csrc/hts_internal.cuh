@@ -25,6 +25,8 @@
 namespace hts {
 
 constexpr int kLevels = HTS_TREE_LEVELS;  // 29 levels: 58 key bits
+constexpr int kMaxSegments = HTS_MAX_SEGMENTS;  // segment id in the top 6 key bits
+constexpr int kSegShift = 2 * kLevels;          // 58
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 // Point record, float32 mode: position as hi + lo float pairs (the pair
@@ -124,6 +126,27 @@ struct hts_ctx {
     int *n_nodes = nullptr;          // device scalar: number of tree nodes
     double *h_pinned = nullptr;      // 8 doubles of pinned host scratch
 
+    // batched embeddings: nseg independent problems in consecutive point ranges
+    int nseg = 1;
+    int64_t *seg_off = nullptr;      // device, nseg + 1 offsets
+    unsigned char *seg_of = nullptr; // device, segment of each point (original order)
+    double *seg_lr = nullptr;        // device, per-segment learning-rate factor
+    double *seg_z = nullptr;         // device, per-segment Z (nseg > 1)
+    int64_t seg_off_h[HTS_MAX_SEGMENTS + 1] = {0};
+
+    // CUDA graph of one iteration (replayed by hts_step when enabled)
+    int use_graphs = 0;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double gkey[5] = {-1, -1, -1, -1, -1};  // theta, exag, lr, momentum, layout version
+    int64_t layout_version = 0;
+    int64_t graph_launches = 0;      // kernels in one captured iteration
+
+    // launch shapes (hts_autotune / hts_set_tuning)
+    int walk_block = 256;            // walk threads per block: 32, 64, 128 or 256
+    int attract_group = 8;           // float32 attraction lanes per row of P: 4, 8, 16 or 32
+
     // CO-SNE term (Sec. 4.3): lambda1 KL + lambda2 (1/n) sum (|x|^2 - |y|^2)^2
     double cosne_l1 = 1.0, cosne_l2 = 0.0;
     double *xsq = nullptr;           // |x_i|^2, n doubles (nullptr: term off)
@@ -157,10 +180,13 @@ void launch_attract(hts_ctx *c);
 void launch_kl_terms(hts_ctx *c);
 void launch_validate_csr(hts_ctx *c, int n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
                          const void *values, int f64);
+void launch_kl_rows(hts_ctx *c, double *a, double *b, double *p);
+void launch_segments_setup(hts_ctx *c);
 // update.cu
 void launch_reduce_z(hts_ctx *c);
 void launch_update(hts_ctx *c, double exag, double lr, double mom, double2 *g_out, int do_step);
 void launch_check_y(hts_ctx *c);
+void launch_segment_sums(hts_ctx *c, const double *v, double *out);
 
 }  // namespace hts
 
@@ -274,6 +300,7 @@ __device__ __forceinline__ DD dd_add(DD a, DD b)
 __device__ __forceinline__ int quad_level(int pref)
 {
     if (pref >= 64) return kLevels;
+    if (pref < 6) return -1;  // keys of different segments: above every segment's root
     int l = (pref - 6) >> 1;
     return l < kLevels ? l : kLevels;
 }

@@ -4,13 +4,13 @@
 //   PoincareMetric), the 32-byte point records, and the radial split
 //   coordinate (disk radius for Eq. EqualEmbeddingLengthsSplitting, cosh of
 //   the hyperbolic radius, (1 + |y|^2) / (1 - |y|^2), for Eq.
-//   EqualAreaSplitting) with the root annulus bounds reduced by atomic
-//   min / max on the bit patterns (exact for non-negative doubles).
+//   EqualAreaSplitting) with the root annulus bounds of each segment reduced
+//   by atomic min / max on the bit patterns (exact for non-negative doubles).
 // make_keys: normalised coordinates rho^ = (c - c_min) / (c_max - c_min),
 //   phi^ = atan2 / 2 pi in [0, 1], each quantised to 29 bits and
 //   interleaved (digit l = 2 * radial bit + angular bit of level l, most
 //   significant first), so that the depth-l cell of the equal-length tree is
-//   the top 2l key bits.  The float64 steps use explicitly rounded
+//   the top 2l key bits below the 6-bit segment id (bits 58..63).  The float64 steps use explicitly rounded
 //   intrinsics so no fused multiply-add changes a quantised bit.
 #include "hts_internal.cuh"
 
@@ -19,18 +19,26 @@ namespace {
 
 constexpr int kBlock = 256;
 
-__global__ void init_minmax_kernel(unsigned long long *mm)
+__global__ void init_minmax_kernel(unsigned long long *mm, int nseg)
 {
-    mm[0] = 0x7FF0000000000000ull;  // +inf
-    mm[1] = 0ull;                   // +0
+    const int s = threadIdx.x;
+    if (s < nseg) {
+        mm[2 * s] = 0x7FF0000000000000ull;  // +inf
+        mm[2 * s + 1] = 0ull;               // +0
+    }
 }
 
+// Per point: records and radial coordinate; per segment: the root annulus
+// [min, max] of the radial coordinate (warp-reduced when a warp's points lie
+// in one segment, which is all but the warps straddling a boundary).
 __global__ void prep_points_kernel(int n, const double2 *__restrict__ y, int split_rule, PointF *pts32,
-                                   PointD *pts64, double *radial, unsigned long long *mm)
+                                   PointD *pts64, double *radial, const unsigned char *__restrict__ seg_of,
+                                   unsigned long long *mm)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double c = 0.0;
     bool ok = i < n;
+    int sg = 0;
     if (ok) {
         double2 p = y[i];
         double n2 = __dadd_rn(__dmul_rn(p.x, p.x), __dmul_rn(p.y, p.y));
@@ -48,31 +56,26 @@ __global__ void prep_points_kernel(int n, const double2 *__restrict__ y, int spl
         if (pts64) pts64[i] = PointD{p.x, p.y, il, 0.0};
         c = split_rule == HTS_EQUAL_AREA ? __ddiv_rn(__dadd_rn(1.0, n2), __dsub_rn(1.0, n2)) : __dsqrt_rn(n2);
         radial[i] = c;
+        if (seg_of) sg = seg_of[i];
     }
-    // block min / max, then one atomic each
-    __shared__ unsigned long long smin[kBlock / 32], smax[kBlock / 32];
     unsigned long long b = (unsigned long long)__double_as_longlong(c);
-    unsigned long long vmin = ok ? b : 0x7FF0000000000000ull;
-    unsigned long long vmax = ok ? b : 0ull;
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long a = __shfl_xor_sync(0xffffffffu, vmin, o);
-        unsigned long long z = __shfl_xor_sync(0xffffffffu, vmax, o);
-        vmin = a < vmin ? a : vmin;
-        vmax = z > vmax ? z : vmax;
-    }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        smin[w] = vmin;
-        smax[w] = vmax;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < kBlock / 32; ++k) {
-            vmin = smin[k] < vmin ? smin[k] : vmin;
-            vmax = smax[k] > vmax ? smax[k] : vmax;
+    const int s0 = __shfl_sync(0xffffffffu, sg, 0);
+    if (__all_sync(0xffffffffu, !ok || sg == s0)) {
+        unsigned long long vmin = ok ? b : 0x7FF0000000000000ull;
+        unsigned long long vmax = ok ? b : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long a = __shfl_xor_sync(0xffffffffu, vmin, o);
+            unsigned long long z = __shfl_xor_sync(0xffffffffu, vmax, o);
+            vmin = a < vmin ? a : vmin;
+            vmax = z > vmax ? z : vmax;
         }
-        atomicMin(&mm[0], vmin);
-        atomicMax(&mm[1], vmax);
+        if ((threadIdx.x & 31) == 0 && vmax >= vmin) {
+            atomicMin(&mm[2 * s0], vmin);
+            atomicMax(&mm[2 * s0 + 1], vmax);
+        }
+    } else if (ok) {
+        atomicMin(&mm[2 * sg], b);
+        atomicMax(&mm[2 * sg + 1], b);
     }
 }
 
@@ -97,12 +100,14 @@ __device__ __forceinline__ uint64_t quantise(double u)
 }
 
 __global__ void make_keys_kernel(int n, const double2 *__restrict__ y, const double *__restrict__ radial,
-                                 const unsigned long long *__restrict__ mm, uint64_t *keys, uint32_t *idx)
+                                 const unsigned char *__restrict__ seg_of, const unsigned long long *__restrict__ mm,
+                                 uint64_t *keys, uint32_t *idx)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double lo = __longlong_as_double((long long)mm[0]);
-    double hi = __longlong_as_double((long long)mm[1]);
+    const int sg = seg_of ? seg_of[i] : 0;
+    double lo = __longlong_as_double((long long)mm[2 * sg]);
+    double hi = __longlong_as_double((long long)mm[2 * sg + 1]);
     double c = radial[i];
     double rh = hi > lo ? __ddiv_rn(__dsub_rn(c, lo), __dsub_rn(hi, lo)) : 0.0;
     double2 p = y[i];
@@ -110,7 +115,7 @@ __global__ void make_keys_kernel(int n, const double2 *__restrict__ y, const dou
     if (phi < 0.0) phi = __dadd_rn(phi, kTwoPi);
     double ph = __ddiv_rn(phi, kTwoPi);
     uint64_t qa = quantise(rh), qb = quantise(ph);
-    keys[i] = (spread_bits(qa) << 1) | spread_bits(qb);
+    keys[i] = ((uint64_t)sg << kSegShift) | (spread_bits(qa) << 1) | spread_bits(qb);
     idx[i] = (uint32_t)i;
 }
 
@@ -119,18 +124,19 @@ __global__ void make_keys_kernel(int n, const double2 *__restrict__ y, const dou
 void launch_prep_points(hts_ctx *c)
 {
     int n = (int)c->n;
-    init_minmax_kernel<<<1, 1, 0, c->stream>>>(c->minmax);
+    init_minmax_kernel<<<1, kMaxSegments, 0, c->stream>>>(c->minmax, c->nseg);
     bool f32 = c->cfg.precision == HTS_FP32_MIXED;
     prep_points_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(
-        n, c->y, c->cfg.split_rule, f32 ? c->pts32 : nullptr, f32 ? nullptr : c->pts64, c->radial, c->minmax);
+        n, c->y, c->cfg.split_rule, f32 ? c->pts32 : nullptr, f32 ? nullptr : c->pts64, c->radial,
+        c->nseg > 1 ? c->seg_of : nullptr, c->minmax);
     c->launches += 2;
 }
 
 void launch_make_keys(hts_ctx *c)
 {
     int n = (int)c->n;
-    make_keys_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(n, c->y, c->radial, c->minmax, c->keys,
-                                                                         c->idx);
+    make_keys_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(
+        n, c->y, c->radial, c->nseg > 1 ? c->seg_of : nullptr, c->minmax, c->keys, c->idx);
     c->launches += 1;
 }
 

@@ -50,13 +50,31 @@ __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int 
     return r;
 }
 
+// Batched embeddings: the sorted points of segment s occupy positions
+// [off[s], off[s+1]) (sorting keeps segments in order), so its tree is the
+// pre-order range [pre[off[s]], pre[off[s+1]]).  A lane is active only inside
+// its own segment's range; lanes of a warp that straddles two segments walk
+// their own trees under the same cursor.
+struct SegView {
+    const uint64_t *keys;   // sorted keys (segment id in the top bits)
+    const int64_t *off;     // segment offsets
+    const int *pre;         // pre-order start position per first point
+};
+
+__device__ __forceinline__ void segment_range(const SegView &sv, int p, int m, int &root, int &end)
+{
+    const int sg = (int)(sv.keys[p] >> kSegShift);
+    root = sv.pre[sv.off[sg]];
+    end = min(sv.pre[sv.off[sg + 1]], m);
+}
+
 // One warp walks for the 32 sorted points of chunk `warp`.
-template <int GF, bool COUNT>
+template <int GF, bool COUNT, bool SEG>
 __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__restrict__ nodes,
                                                 const int *__restrict__ n_nodes,
                                                 const PointF *__restrict__ spts,
                                                 const uint32_t *__restrict__ idx, double2 *frep, double *zi,
-                                                unsigned long long *counters, int *status)
+                                                unsigned long long *counters, const SegView sv)
 {
     const int lane = threadIdx.x & 31;
     const int p = warp * 32 + lane;
@@ -65,12 +83,15 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
     const float twoil = 2.0f * q.il;
     float rx = 0.f, ry = 0.f, rs = 0.f, z = 0.f;
     const int m = min(*n_nodes, 2 * n);
-    int resume = valid ? 0 : INT_MAX;
-    int node = 0;
+    int root = 0, end = m;
+    if (SEG) segment_range(sv, valid ? p : n - 1, m, root, end);
+    int resume = valid ? root : INT_MAX;
+    int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : 0;  // lane 0 holds the first segment
+    const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : m;
     unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
-    while (node < m) {
+    while (node < stop) {
         const NodeF c = load_node(nodes, node);
-        const bool active = node >= resume;
+        const bool active = node >= resume && (!SEG || node < end);
         int next = node + 1;
         if (c.count >= 2) {
             float dx = (q.xh - c.xh) + (q.xl - c.xl);
@@ -147,27 +168,28 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
     }
 }
 
-// One warp per chunk of 32 sorted points; the 8 warps of a block take
-// consecutive chunks, so their walks share node data in L1.
-template <int GF, bool COUNT>
+// One warp per chunk of 32 sorted points; the warps of a block (blockDim.x /
+// 32 <= kWalkBlock / 32, picked by the autotuner) take consecutive chunks, so
+// their walks share node data in L1.  The block size does not change results.
+template <int GF, bool COUNT, bool SEG>
 __global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF *__restrict__ nodes,
                                                               const int *__restrict__ n_nodes,
                                                               const PointF *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              int *status)
+                                                              const SegView sv)
 {
-    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp * 32 >= n) return;
-    walk_f32_chunk<GF, COUNT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
+    walk_f32_chunk<GF, COUNT, SEG>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv);
 }
 
-template <int GF, bool COUNT>
+template <int GF, bool COUNT, bool SEG>
 __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__restrict__ nodes,
                                                 const int *__restrict__ n_nodes,
                                                 const PointD *__restrict__ spts,
                                                 const uint32_t *__restrict__ idx, double2 *frep, double *zi,
-                                                unsigned long long *counters, int *status)
+                                                unsigned long long *counters, const SegView sv)
 {
     const int lane = threadIdx.x & 31;
     const int p = warp * 32 + lane;
@@ -176,12 +198,15 @@ __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__r
     const double twoil = 2.0 * q.il;
     double rx = 0, ry = 0, rs = 0, z = 0;
     const int m = min(*n_nodes, 2 * n);
-    int resume = valid ? 0 : INT_MAX;
-    int node = 0;
+    int root = 0, end = m;
+    if (SEG) segment_range(sv, valid ? p : n - 1, m, root, end);
+    int resume = valid ? root : INT_MAX;
+    int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : 0;
+    const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : m;
     unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
-    while (node < m) {
+    while (node < stop) {
         const NodeD c = nodes[node];
-        const bool active = node >= resume;
+        const bool active = node >= resume && (!SEG || node < end);
         int next = node + 1;
         if (c.count >= 2) {
             double dx = q.x - c.x, dy = q.y - c.y;
@@ -253,19 +278,18 @@ __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__r
     }
 }
 
-// One warp per chunk of 32 sorted points; the 8 warps of a block take
-// consecutive chunks, so their walks share node data in L1.
-template <int GF, bool COUNT>
+// As walk_f32_kernel, in float64.
+template <int GF, bool COUNT, bool SEG>
 __global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD *__restrict__ nodes,
                                                               const int *__restrict__ n_nodes,
                                                               const PointD *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              int *status)
+                                                              const SegView sv)
 {
-    const int warp = (blockIdx.x * kWalkBlock + threadIdx.x) >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp * 32 >= n) return;
-    walk_f64_chunk<GF, COUNT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, status);
+    walk_f64_chunk<GF, COUNT, SEG>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv);
 }
 
 
@@ -273,20 +297,32 @@ __global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD
 // shared memory, every pair j != i.
 template <int GF>
 __global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(int n, const PointF *__restrict__ pts, double2 *frep,
-                                                                double *zi)
+                                                                double *zi, const unsigned char *__restrict__ seg_of,
+                                                                const int64_t *__restrict__ seg_off)
 {
     __shared__ PointF tile[kExactBlock];
     const int i = blockIdx.x * kExactBlock + threadIdx.x;
+    // own segment [jlo, jhi) and the union over the block's threads [blo, bhi)
+    int jlo = 0, jhi = n, blo = 0, bhi = n;
+    if (seg_of) {
+        const int first = blockIdx.x * kExactBlock, last = min(first + kExactBlock, n) - 1;
+        const int si = seg_of[i < n ? i : n - 1];
+        jlo = (int)seg_off[si];
+        jhi = (int)seg_off[si + 1];
+        blo = (int)seg_off[seg_of[first]];
+        bhi = (int)seg_off[seg_of[last] + 1];
+    }
     const PointF q = pts[i < n ? i : n - 1];
     const float twoil = 2.0f * q.il;
     float rx = 0.f, ry = 0.f, rs = 0.f, z = 0.f;
-    for (int base = 0; base < n; base += kExactBlock) {
+    for (int base = blo; base < bhi; base += kExactBlock) {
         int j = base + threadIdx.x;
-        if (j < n) tile[threadIdx.x] = pts[j];
+        if (j < bhi) tile[threadIdx.x] = pts[j];
         __syncthreads();
-        const int cnt = min(kExactBlock, n - base);
+        const int cnt = min(kExactBlock, bhi - base);
         for (int k = 0; k < cnt; ++k) {
-            if (base + k == i) continue;
+            const int jj = base + k;
+            if (jj == i || jj < jlo || jj >= jhi) continue;
             const PointF o = tile[k];
             float dx = (q.xh - o.xh) + (q.xl - o.xl);
             float dy = (q.yh - o.yh) + (q.yl - o.yl);
@@ -311,20 +347,32 @@ __global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(int n, const Poi
 
 template <int GF>
 __global__ void __launch_bounds__(kExactBlock) exact_f64_kernel(int n, const PointD *__restrict__ pts, double2 *frep,
-                                                                double *zi)
+                                                                double *zi, const unsigned char *__restrict__ seg_of,
+                                                                const int64_t *__restrict__ seg_off)
 {
     __shared__ PointD tile[kExactBlock];
     const int i = blockIdx.x * kExactBlock + threadIdx.x;
+    // own segment [jlo, jhi) and the union over the block's threads [blo, bhi)
+    int jlo = 0, jhi = n, blo = 0, bhi = n;
+    if (seg_of) {
+        const int first = blockIdx.x * kExactBlock, last = min(first + kExactBlock, n) - 1;
+        const int si = seg_of[i < n ? i : n - 1];
+        jlo = (int)seg_off[si];
+        jhi = (int)seg_off[si + 1];
+        blo = (int)seg_off[seg_of[first]];
+        bhi = (int)seg_off[seg_of[last] + 1];
+    }
     const PointD q = pts[i < n ? i : n - 1];
     const double twoil = 2.0 * q.il;
     double rx = 0, ry = 0, rs = 0, z = 0;
-    for (int base = 0; base < n; base += kExactBlock) {
+    for (int base = blo; base < bhi; base += kExactBlock) {
         int j = base + threadIdx.x;
-        if (j < n) tile[threadIdx.x] = pts[j];
+        if (j < bhi) tile[threadIdx.x] = pts[j];
         __syncthreads();
-        const int cnt = min(kExactBlock, n - base);
+        const int cnt = min(kExactBlock, bhi - base);
         for (int k = 0; k < cnt; ++k) {
-            if (base + k == i) continue;
+            const int jj = base + k;
+            if (jj == i || jj < jlo || jj >= jhi) continue;
             const PointD o = tile[k];
             double dx = q.x - o.x, dy = q.y - o.y;
             double s = fma(dx, dx, dy * dy);
@@ -350,47 +398,49 @@ void launch_walk(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int warps = (n + 31) / 32;
-    const int blocks = (warps * 32 + kWalkBlock - 1) / kWalkBlock;
+    const int wb = c->walk_block;  // 32 .. kWalkBlock threads, a multiple of 32
+    const int blocks = (warps * 32 + wb - 1) / wb;
     const bool cnt = c->counters_on != 0;  // counters accumulate while enabled
+    const bool seg = c->nseg > 1;
+    const SegView sv{c->keys, c->seg_off, c->pre};
     c->launches += 1;
-    if (c->cfg.precision == HTS_FP32_MIXED) {
-#define HTS_WALK(GF, CT) \
-    walk_f32_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes32, c->n_nodes, c->spts32, c->idx, \
-                                                                  c->frep, c->zi, c->counters, c->status)
-        if (c->cfg.grad_form == HTS_EXACT_KL) {
-            if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
-        } else {
-            if (cnt) HTS_WALK(1, true); else HTS_WALK(1, false);
-        }
-#undef HTS_WALK
-    } else {
-#define HTS_WALK(GF, CT) \
-    walk_f64_kernel<GF, CT><<<blocks, kWalkBlock, 0, c->stream>>>(n, c->nodes64, c->n_nodes, c->spts64, c->idx, \
-                                                                  c->frep, c->zi, c->counters, c->status)
-        if (c->cfg.grad_form == HTS_EXACT_KL) {
-            if (cnt) HTS_WALK(0, true); else HTS_WALK(0, false);
-        } else {
-            if (cnt) HTS_WALK(1, true); else HTS_WALK(1, false);
-        }
-#undef HTS_WALK
+#define HTS_WALK(P, NODES, SPTS, GF, CT, SG)                                                             \
+    walk_##P##_kernel<GF, CT, SG><<<blocks, wb, 0, c->stream>>>(n, NODES, c->n_nodes, SPTS, c->idx, \
+                                                                         c->frep, c->zi, c->counters, sv)
+#define HTS_WALK_ALL(P, NODES, SPTS)                                                   \
+    if (c->cfg.grad_form == HTS_EXACT_KL) {                                             \
+        if (cnt) { if (seg) HTS_WALK(P, NODES, SPTS, 0, true, true); else HTS_WALK(P, NODES, SPTS, 0, true, false); } \
+        else { if (seg) HTS_WALK(P, NODES, SPTS, 0, false, true); else HTS_WALK(P, NODES, SPTS, 0, false, false); } \
+    } else {                                                                            \
+        if (cnt) { if (seg) HTS_WALK(P, NODES, SPTS, 1, true, true); else HTS_WALK(P, NODES, SPTS, 1, true, false); } \
+        else { if (seg) HTS_WALK(P, NODES, SPTS, 1, false, true); else HTS_WALK(P, NODES, SPTS, 1, false, false); } \
     }
+    if (c->cfg.precision == HTS_FP32_MIXED) {
+        HTS_WALK_ALL(f32, c->nodes32, c->spts32)
+    } else {
+        HTS_WALK_ALL(f64, c->nodes64, c->spts64)
+    }
+#undef HTS_WALK_ALL
+#undef HTS_WALK
 }
 
 void launch_exact(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int blocks = (n + kExactBlock - 1) / kExactBlock;
+    const unsigned char *so = c->nseg > 1 ? c->seg_of : nullptr;
+    const int64_t *sf = c->seg_off;
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
         if (c->cfg.grad_form == HTS_EXACT_KL)
-            exact_f32_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi);
+            exact_f32_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi, so, sf);
         else
-            exact_f32_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi);
+            exact_f32_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi, so, sf);
     } else {
         if (c->cfg.grad_form == HTS_EXACT_KL)
-            exact_f64_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi);
+            exact_f64_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi, so, sf);
         else
-            exact_f64_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi);
+            exact_f64_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi, so, sf);
     }
 }
 

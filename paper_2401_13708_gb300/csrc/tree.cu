@@ -373,9 +373,12 @@ __global__ void emit_kernel(EmitArgs A)
         double cx = __ddiv_rn(mx, __dadd_rn(1.0, sq)), cy = __ddiv_rn(my, __dadd_rn(1.0, sq));
         double beta = __dsub_rn(1.0, __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)));
         double il = 1.0 / beta;
-        double lob = __longlong_as_double((long long)A.mm[0]);
-        double hib = __longlong_as_double((long long)A.mm[1]);
-        uint64_t prefix = ell > 0 ? (A.keys[lo] >> (2 * (kLevels - ell))) : 0ull;
+        const uint64_t key = A.keys[lo];
+        const int seg = (int)(key >> kSegShift);  // segment: its own root annulus
+        double lob = __longlong_as_double((long long)A.mm[2 * seg]);
+        double hib = __longlong_as_double((long long)A.mm[2 * seg + 1]);
+        const uint64_t kb = key & ((1ull << kSegShift) - 1);
+        uint64_t prefix = ell > 0 ? (kb >> (2 * (kLevels - ell))) : 0ull;
         // float64 geometry for the float64 walk and for exports; float32 otherwise
         const bool geo64 = A.nodes64 != nullptr || A.ex.depth != nullptr;
         double rc = HUGE_VAL, thr = HUGE_VAL;
@@ -474,7 +477,7 @@ __global__ void emit_kernel(EmitArgs A)
             uint32_t i = A.idx[k];
             double2 q = A.y[i];
             A.ex.depth[pos] = depth;
-            A.ex.prefix[pos] = depth > 0 ? (A.keys[k] >> (2 * (kLevels - depth))) : 0ull;
+            A.ex.prefix[pos] = depth > 0 ? ((A.keys[k] & ((1ull << kSegShift) - 1)) >> (2 * (kLevels - depth))) : 0ull;
             A.ex.count[pos] = 1;
             A.ex.first[pos] = i;
             A.ex.ycell[2 * pos] = q.x;

@@ -53,6 +53,23 @@ __global__ void __launch_bounds__(kRedBlocks) final_sum_kernel(const double *__r
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// Per-segment sum of v over [off[s], off[s+1]), one block per segment.
+__global__ void __launch_bounds__(1024) segment_sum_kernel(const double *__restrict__ v,
+                                                          const int64_t *__restrict__ off, double *out)
+{
+    __shared__ double sh[1024];
+    const int64_t lo = off[blockIdx.x], hi = off[blockIdx.x + 1];
+    double a = 0;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += 1024) a += v[k];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
 struct UpdateArgs {
     int n;
     double2 *y, *vel, *gains;
@@ -64,13 +81,17 @@ struct UpdateArgs {
     int *status;
     const double *xsq;  // CO-SNE |x_i|^2 (nullptr: off)
     double l1, l2;
+    const unsigned char *seg_of;  // batched: segment of each point (nullptr: one problem)
+    const double *seg_lr;         // batched: learning-rate factor per segment
+    const int64_t *seg_off;       // batched: segment offsets (CO-SNE uses the segment's n)
 };
 
 __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
 {
     const int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= A.n) return;
-    const double Z = *A.Z;
+    const int sg = A.seg_of ? A.seg_of[i] : 0;
+    const double Z = A.Z[sg];
     const double invZ = Z > 0.0 ? 1.0 / Z : 0.0;
     const double2 fa = A.fattr[i], fr = A.frep[i];
     double gx = 4.0 * (A.exag * fa.x - fr.x * invZ);
@@ -78,7 +99,8 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
     double2 p = A.y[i];
     const double n2 = p.x * p.x + p.y * p.y;
     if (A.xsq) {  // CO-SNE: lambda1 g_KL - (4 lambda2 / n)(|x|^2 - |y|^2) y
-        const double c = 4.0 * A.l2 / (double)A.n * (A.xsq[i] - n2);
+        const double ns = A.seg_of ? (double)(A.seg_off[sg + 1] - A.seg_off[sg]) : (double)A.n;
+        const double c = 4.0 * A.l2 / ns * (A.xsq[i] - n2);
         gx = A.l1 * gx - c * p.x;
         gy = A.l1 * gy - c * p.y;
     }
@@ -98,8 +120,9 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
         kx = gn.x;
         ky = gn.y;
     }
-    v.x = A.mom * v.x - A.lr * kx * (gx * sc);
-    v.y = A.mom * v.y - A.lr * ky * (gy * sc);
+    const double lr = A.seg_of ? A.lr * A.seg_lr[sg] : A.lr;
+    v.x = A.mom * v.x - lr * kx * (gx * sc);
+    v.y = A.mom * v.y - lr * ky * (gy * sc);
     const double nv = sqrt(v.x * v.x + v.y * v.y);
     double2 q = p;
     if (nv > 0.0) {
@@ -138,6 +161,11 @@ __global__ void check_y_kernel(int n, const double2 *__restrict__ y, int *status
 
 void launch_reduce_z(hts_ctx *c)
 {
+    if (c->nseg > 1) {  // one block per segment, fixed order
+        segment_sum_kernel<<<c->nseg, 1024, 0, c->stream>>>(c->zi, c->seg_off, c->seg_z);
+        c->launches += 1;
+        return;
+    }
     double *partial = c->red_tmp;  // >= kRedBlocks doubles
     partial_sum_kernel<<<kRedBlocks, kBlock, 0, c->stream>>>((int)c->n, c->zi, partial);
     final_sum_kernel<<<1, kRedBlocks, 0, c->stream>>>(partial, c->dscal);
@@ -153,7 +181,10 @@ void launch_update(hts_ctx *c, double exag, double lr, double mom, double2 *g_ou
     A.gains = c->gains;
     A.fattr = c->fattr;
     A.frep = c->frep;
-    A.Z = c->dscal;
+    A.Z = c->nseg > 1 ? c->seg_z : c->dscal;
+    A.seg_of = c->nseg > 1 ? c->seg_of : nullptr;
+    A.seg_lr = c->seg_lr;
+    A.seg_off = c->seg_off;
     A.exag = exag;
     A.lr = lr;
     A.mom = mom;
@@ -167,6 +198,12 @@ void launch_update(hts_ctx *c, double exag, double lr, double mom, double2 *g_ou
     A.l1 = c->cosne_l1;
     A.l2 = c->cosne_l2;
     update_kernel<<<(A.n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(A);
+    c->launches += 1;
+}
+
+void launch_segment_sums(hts_ctx *c, const double *v, double *out)
+{
+    segment_sum_kernel<<<c->nseg, 1024, 0, c->stream>>>(v, c->seg_off, out);
     c->launches += 1;
 }
 

@@ -47,6 +47,7 @@ __all__ = [
     "initial_embedding",
     "spread_embedding",
     "make_config",
+    "make_batched",
     "CONFIG_NAMES",
 ]
 
@@ -340,3 +341,39 @@ def make_config(cfg: int, seed: int = 0, device: str = "cpu", n: Optional[int] =
     nn = int(indptr.shape[0] - 1)
     return Workload(name=CONFIG_NAMES[cfg], n=nn, indptr=indptr, indices=indices, values=values,
                     y0=initial_embedding(nn, seed), labels=lab, perplexity=perplexity)
+
+
+def make_batched(count: int = 64, seed: int = 0, device: str = "cpu", n_lo: int = 500, n_hi: int = 20000,
+                 d: int = 50, value_dtype=np.float32) -> Workload:
+    """`count` independent mixtures as one block-diagonal problem.
+
+    Each embedding s is a Gaussian mixture of n_s points in D=d with its own
+    component count and perplexity (batched_mixtures); its P is the usual
+    symmetric (P_c + P_c^T) / (2 n_s) over its own points, so every block sums
+    to 1.  extra["offsets"] holds the int64 segment boundaries (count + 1),
+    extra["params"] the (n, components, perplexity, seed) of each embedding.
+    """
+    params = batched_mixtures(count, seed, n_lo, n_hi, d)
+    ips, ids, vals, ys, labs, offs = [], [], [], [], [], [0]
+    for (n, comps, perp, sub) in params:
+        x, lab = gaussian_mixture(n, d, comps, sub)
+        ip, ix, v = affinities_csr(x, perp, None, device, value_dtype)
+        base = offs[-1]
+        ips.append(np.asarray(ip, dtype=np.int64))
+        ids.append(np.asarray(ix, dtype=np.int64) + base)
+        vals.append(np.asarray(v))
+        ys.append(initial_embedding(n, sub))
+        labs.append(np.asarray(lab))
+        offs.append(base + n)
+    nnz_base = 0
+    indptr_parts = []
+    for ip in ips:
+        indptr_parts.append(ip[:-1] + nnz_base)
+        nnz_base += int(ip[-1])
+    indptr = np.concatenate(indptr_parts + [np.array([nnz_base], dtype=np.int64)]).astype(np.int64)
+    indices = np.concatenate(ids).astype(np.int32)
+    values = np.concatenate(vals).astype(value_dtype)
+    nn = offs[-1]
+    return Workload(name=f"{count} batched mixtures N~logU({n_lo},{n_hi})", n=nn, indptr=indptr, indices=indices,
+                    values=values, y0=np.concatenate(ys), labels=np.concatenate(labs), perplexity=float("nan"),
+                    extra={"offsets": np.asarray(offs, dtype=np.int64), "params": params})
