@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--sample-rows", type=int, default=10000)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cache", default="", help="directory to keep the generated workload in (reused if present)")
+    ap.add_argument("--shapes", default="",
+                    help="walk threads per block,attraction lanes per row (e.g. 256,8) instead of the autotuner")
     ap.add_argument("--profile-only", action="store_true",
                     help="FP32-mixed steps only (for a profiler): no FP64 arm, e2e or oracle")
     return ap.parse_args()
@@ -285,6 +287,11 @@ def run_ours(args, rank, world, local):
         g32[name] = t.grad(theta, 1.0)
     t.set_Y(y0)
     protocol(t, 0, W, theta, lr)
+    if args.shapes:                                # fixed launch shapes (e.g. for a profiler run)
+        t.set_tuning(*[int(v) for v in args.shapes.split(",")])
+        walk_block, attract_lanes = t.get_tuning()
+    else:                                          # launch shapes for this problem (Y unchanged)
+        walk_block, attract_lanes = t.autotune(theta, 3)
     y_s = t.get_Y()                                # state at the start of the timed segment
     v_s, _, _ = t.get_state()
     if args.profile_only:
@@ -357,17 +364,15 @@ def run_ours(args, rank, world, local):
     k_e2e = max(3, min(K, 20))
     yh = torch.from_numpy(np.ascontiguousarray(y_s)).pin_memory()
     vh = torch.from_numpy(np.ascontiguousarray(v_s)).pin_memory()
-    yv, vv = yh.numpy(), vh.numpy()
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for k in range(k_e2e):
         t.set_Y(yh)
-        t.set_state(vv, None, 0)
+        t.set_state(vh, None, 0)
         protocol(t, W + k, 1, theta, lr)
-        t.get_Y(yv)
-        v_now, _, _ = t.get_state()
-        vv[...] = v_now
+        t.get_Y(yh)
+        t.get_state(vh, with_gains=False)
     torch.cuda.synchronize()
     barrier(world)
     dt = max_over_ranks(time.perf_counter() - t0, world)
@@ -422,7 +427,9 @@ def run_ours(args, rank, world, local):
                    "protocol": f"iterations {W}..{W + K - 1} of 250 (exaggeration 12, momentum 0.5) + 750 "
                                f"(1, 0.8), lr = N/12000, Y0 ~ N(0, 1e-4 I)",
                    "l2": "inputs larger than L2 (CSR ~%.2f GB)" % (w.nnz * 8 / 1e9),
-                   "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1)},
+                   "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1),
+                   "launch_shapes": {"walk_threads_per_block": walk_block, "attract_lanes_per_row": attract_lanes,
+                                     "chosen_by": "--shapes" if args.shapes else "hts_autotune after the warm-up"}},
         "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
                      "fp32_mixed_ms_per_step_same_segment": ms32_seg / k64,
                      "fp32_mixed_speedup": ms64 / ms32_seg},

@@ -120,8 +120,11 @@ HTS_API int hts_set_P(hts_ctx *ctx, int64_t n, int64_t nnz, const int64_t *indpt
 
 /* Copy the embedding Y (n x 2 float64) into the context and reset the
  * velocity to 0 and the gains to 1.  Every point must satisfy |y| < 1 and be
- * finite.  Errors: HTS_EINVAL, HTS_ESHAPE (n differs from P), HTS_EDOMAIN,
- * HTS_EOOM, HTS_ECUDA. */
+ * finite; this is checked on the device after the copy (host and device
+ * inputs alike), and the call returns once the copy is complete.  On
+ * HTS_EDOMAIN the context holds no Y until the next successful call.
+ * Errors: HTS_EINVAL, HTS_ESHAPE (n differs from P), HTS_EDOMAIN, HTS_EOOM,
+ * HTS_ECUDA. */
 HTS_API int hts_set_Y(hts_ctx *ctx, int64_t n, const double *y, int where);
 
 /* Run n_iter gradient-descent iterations (Sec. 5.1): each builds the tree

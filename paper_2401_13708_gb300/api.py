@@ -247,20 +247,33 @@ class HyperbolicTSNE:
         self._check(self._lib.hts_get_profile(self._ctx, ms.ctypes.data_as(C.c_void_p), C.byref(it)))
         return dict(zip(self.PHASES, ms.tolist())), int(it.value)
 
-    def get_state(self):
-        vel = np.empty((self.n, 2))
-        gains = np.empty((self.n, 2))
+    def get_state(self, vel=None, gains=None, with_gains: bool = True):
+        """(velocity, gains, iterations run).  `vel` / `gains` may be output
+        arrays (numpy, or torch host or CUDA tensors, n x 2 float64, all in the
+        same memory); with_gains=False skips the gains (returned as None)."""
+        if vel is None:
+            vel = np.empty((self.n, 2))
+        if gains is None and with_gains:
+            gains = np.empty((self.n, 2))
+        pv, wv, kv = _arg(vel, np.float64)
+        pg, wg, kg = (None, wv, None) if gains is None else _arg(gains, np.float64)
+        if wv != wg:
+            raise ValueError("vel and gains must both be host or both device memory")
         it = C.c_int64(0)
-        self._check(self._lib.hts_get_state(self._ctx, vel.ctypes.data_as(C.c_void_p),
-                                            gains.ctypes.data_as(C.c_void_p), C.byref(it), HOST))
-        return vel, gains, int(it.value)
+        self._check(self._lib.hts_get_state(self._ctx, pv, pg, C.byref(it), wv))
+        out_v = vel if not isinstance(kv, np.ndarray) or kv is vel else kv
+        out_g = gains if kg is None or not isinstance(kg, np.ndarray) or kg is gains else kg
+        return out_v, out_g, int(it.value)
 
     def set_state(self, vel=None, gains=None, iters: int = 0):
-        pv = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
-        pg = None if gains is None else np.ascontiguousarray(gains, dtype=np.float64)
-        self._check(self._lib.hts_set_state(self._ctx, None if pv is None else pv.ctypes.data_as(C.c_void_p),
-                                            None if pg is None else pg.ctypes.data_as(C.c_void_p), int(iters),
-                                            HOST))
+        """Restore velocity and / or gains (None leaves a part unchanged)."""
+        pv, wv, kv = (None, None, None) if vel is None else _arg(vel, np.float64)
+        pg, wg, kg = (None, None, None) if gains is None else _arg(gains, np.float64)
+        if wv is not None and wg is not None and wv != wg:
+            raise ValueError("vel and gains must both be host or both device memory")
+        where = wv if wv is not None else (wg if wg is not None else HOST)
+        self._check(self._lib.hts_set_state(self._ctx, pv, pg, int(iters), where))
+        del kv, kg
 
     def sizes(self):
         n, nnz = C.c_int64(0), C.c_int64(0)

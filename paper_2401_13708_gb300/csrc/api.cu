@@ -128,7 +128,7 @@ int ensure_points(hts_ctx *c, int64_t n)
     AL(c->bn_pref, N);
     AL(c->bn_flag, N);
     AL(c->bn_quad, N);
-    AL(c->bn_sum, 6 * (N + 1));  // double-double prefix sums (n + 1 entries)
+    AL(c->bn_sum, 6 * (N + 1));  // 3 x 128-bit fixed-point prefix sums (n + 1 entries, 48 B each)
     AL(c->cnt, N + 1);
     AL(c->pre, N + 1);
     const int64_t tiles = ((int64_t)N + 4095) / 4096;
@@ -161,42 +161,67 @@ int status_error(hts_ctx *c, int st)
 }
 
 constexpr int kPhases = 6;  // keys, sort, tree, walk/exact, attract, Z + update
+constexpr int kEvents = kPhases + 3;  // per iteration: 6 marks on the main stream, 2 on the side stream
+constexpr int kAttractAfter = 0;      // stage after which the attraction forks: 0 prep, 1 keys, 2 sort, 3 tree
 
 // Repulsion, attraction and Z for the current Y (results in frep, zi, fattr,
-// dscal[0]).  With `ev` (kPhases + 1 events) the phase boundaries are recorded.
+// dscal[0] / seg_z).  The attractive sum needs only the point records, so it
+// runs on the side stream (lowest priority) from the stage kAttractAfter to
+// the Z reduction, overlapping the key / sort / tree / walk kernels.  With `ev` (kEvents events)
+// the stage boundaries are recorded: ev[0..4] and ev[6] on the main stream
+// (start, after keys, sort, tree, walk / exact; ev[6] after the update is
+// recorded by the caller), ev[7..8] around the attractive sum.
 int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
 {
 #define MARK(k) \
     if (ev) CK(cudaEventRecord(ev[k], c->stream))
+    const bool attract = c->nnz > 0;
+    // fork: the side stream waits for the point records (and for the stages
+    // before kAttractAfter, so that it does not hold SMs they need)
+    auto fork_attract = [&]() -> int {
+        CK(cudaEventRecord(c->aev_fork, c->stream));
+        CK(cudaStreamWaitEvent(c->astream, c->aev_fork, 0));
+        cudaStream_t keep = c->stream;
+        c->stream = c->astream;
+        if (ev) CK(cudaEventRecord(ev[7], c->astream));
+        launch_attract(c);
+        c->stream = keep;
+        LAUNCHED("attract");
+        if (ev) CK(cudaEventRecord(ev[8], c->astream));
+        CK(cudaEventRecord(c->aev_join, c->astream));
+        return HTS_OK;
+    };
+    int r = HTS_OK;
     MARK(0);
     launch_prep_points(c);
     LAUNCHED("prep_points");
+    if (!attract) CK(cudaMemsetAsync(c->fattr, 0, sizeof(double2) * (size_t)c->n, c->stream));
     if (theta == 0.0) {
+        if (attract && (r = fork_attract())) return r;
         MARK(1);
         MARK(2);
         MARK(3);
         launch_exact(c);
         LAUNCHED("exact");
     } else {
+        if (attract && kAttractAfter == 0 && (r = fork_attract())) return r;
         launch_make_keys(c);
         LAUNCHED("make_keys");
         MARK(1);
+        if (attract && kAttractAfter == 1 && (r = fork_attract())) return r;
         launch_sort_pairs(c);
         LAUNCHED("sort");
         MARK(2);
+        if (attract && kAttractAfter == 2 && (r = fork_attract())) return r;
         launch_build_tree(c, theta, nullptr);
         LAUNCHED("build_tree");
         MARK(3);
+        if (attract && kAttractAfter == 3 && (r = fork_attract())) return r;
         launch_walk(c);
         LAUNCHED("walk");
     }
     MARK(4);
-    if (c->nnz > 0) {
-        launch_attract(c);
-        LAUNCHED("attract");
-    } else {
-        CK(cudaMemsetAsync(c->fattr, 0, sizeof(double2) * (size_t)c->n, c->stream));
-    }
+    if (attract) CK(cudaStreamWaitEvent(c->stream, c->aev_join, 0));  // join
     MARK(5);
     launch_reduce_z(c);
     LAUNCHED("reduce_z");
@@ -207,9 +232,9 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
 int ensure_events(hts_ctx *c, int slots)
 {
     if (slots <= c->event_slots) return HTS_OK;
-    cudaEvent_t *ev = new cudaEvent_t[(size_t)slots * (kPhases + 1)];
-    for (int k = 0; k < c->event_slots * (kPhases + 1); ++k) ev[k] = c->events[k];
-    for (int k = c->event_slots * (kPhases + 1); k < slots * (kPhases + 1); ++k) CK(cudaEventCreate(&ev[k]));
+    cudaEvent_t *ev = new cudaEvent_t[(size_t)slots * kEvents];
+    for (int k = 0; k < c->event_slots * kEvents; ++k) ev[k] = c->events[k];
+    for (int k = c->event_slots * kEvents; k < slots * kEvents; ++k) CK(cudaEventCreate(&ev[k]));
     delete[] c->events;
     c->events = ev;
     c->event_slots = slots;
@@ -259,7 +284,9 @@ int capture_iteration(hts_ctx *c, double theta, double exag, double lr, double m
     if (c->gexec && memcmp(key, c->gkey, sizeof(key)) == 0) return HTS_OK;
     drop_graph(c);
     if (!c->gstream) {
-        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&c->gstream, cudaStreamNonBlocking, greatest));
         CK(cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming));
     }
@@ -281,7 +308,7 @@ int capture_iteration(hts_ctx *c, double theta, double exag, double lr, double m
         if (g) cudaGraphDestroy(g);
         return r ? r : cuda_fail(c, e, "cudaStreamEndCapture");
     }
-    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    e = cudaGraphInstantiate(&c->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         c->gexec = nullptr;
@@ -392,10 +419,21 @@ int hts_create(hts_ctx **out, const hts_config *cfg)
         return HTS_ECUDA;
     }
     c->sm_count = prop.multiProcessorCount;
-    if (dalloc(c, &c->minmax, 2 * kMaxSegments) || dalloc(c, &c->dscal, 8) || dalloc(c, &c->status, 1) ||
+    if (dalloc(c, &c->minmax, 2 * kMaxSegments + 2) || dalloc(c, &c->dscal, 8) || dalloc(c, &c->status, 1) ||
         dalloc(c, &c->counters, 4) || cudaMallocHost((void **)&c->h_pinned, 8 * sizeof(double)) != cudaSuccess) {
         hts_destroy(c);
         return HTS_EOOM;
+    }
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (cudaStreamCreateWithPriority(&c->astream, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->pstream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->aev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->aev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->pev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->pev_out, cudaEventDisableTiming) != cudaSuccess) {
+        hts_destroy(c);
+        return HTS_ECUDA;
     }
     cudaMemset(c->counters, 0, 4 * sizeof(unsigned long long));
     cudaMemset(c->status, 0, sizeof(int));
@@ -426,8 +464,20 @@ void hts_destroy(hts_ctx *c)
     }
     if (c->gev_in) cudaEventDestroy(c->gev_in);
     if (c->gev_out) cudaEventDestroy(c->gev_out);
+    if (c->astream) {
+        cudaStreamSynchronize(c->astream);
+        cudaStreamDestroy(c->astream);
+    }
+    if (c->pstream) {
+        cudaStreamSynchronize(c->pstream);
+        cudaStreamDestroy(c->pstream);
+    }
+    if (c->aev_fork) cudaEventDestroy(c->aev_fork);
+    if (c->aev_join) cudaEventDestroy(c->aev_join);
+    if (c->pev_in) cudaEventDestroy(c->pev_in);
+    if (c->pev_out) cudaEventDestroy(c->pev_out);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
-    for (int k = 0; k < c->event_slots * (kPhases + 1); ++k) cudaEventDestroy(c->events[k]);
+    for (int k = 0; k < c->event_slots * kEvents; ++k) cudaEventDestroy(c->events[k]);
     delete[] c->events;
     delete c;
 }
@@ -545,15 +595,7 @@ int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
     if (c->have_P && n != c->n) return fail(c, HTS_ESHAPE, "hts_set_Y: n differs from the n of P");
     int r = set_device(c);
     if (r) return r;
-    if (where == HTS_HOST) {
-        for (int64_t i = 0; i < n; ++i) {
-            double a = y[2 * i], b = y[2 * i + 1];
-            if (!isfinite(a) || !isfinite(b) || !(a * a + b * b < 1.0))
-                return fail(c, HTS_EDOMAIN, "hts_set_Y: a point has |y| >= 1 or a non-finite coordinate");
-        }
-    } else if (n > 0 && (r = check_device_ptr(c, y))) {
-        return r;
-    }
+    if (where == HTS_DEVICE && n > 0 && (r = check_device_ptr(c, y))) return r;
     if (c->xsq && n != c->n) {
         dfree(&c->xsq);  // the per-point term no longer matches
         c->cosne_l1 = 1.0;
@@ -568,17 +610,17 @@ int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
                            where == HTS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
         fill_state_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->vel, c->gains);
         LAUNCHED("fill_state");
-        if (where == HTS_DEVICE) {
-            CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
-            c->n = n;
-            launch_check_y(c);
-            LAUNCHED("check_y");
-            int st = 0;
-            if ((r = read_status(c, &st))) return r;
-            if (st) {
-                c->have_Y = false;
-                return status_error(c, st);
-            }
+        // host and device inputs alike are checked on the device (one pass,
+        // no host loop over the points); the status read also completes the copy
+        CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        c->n = n;
+        launch_check_y(c);
+        LAUNCHED("check_y");
+        int st = 0;
+        if ((r = read_status(c, &st))) return r;
+        if (st) {
+            c->have_Y = false;
+            return status_error(c, st);
         }
     }
     c->n = n;
@@ -609,22 +651,36 @@ int hts_step(hts_ctx *c, int n_iter, double theta, double exaggeration, double l
         CK(cudaStreamWaitEvent(c->stream, c->gev_out, 0));
         c->launches += c->graph_launches * n_iter;
     } else {
-        for (int it = 0; it < n_iter; ++it) {
-            cudaEvent_t *ev = it < prof ? c->events + (size_t)it * (kPhases + 1) : nullptr;
-            if ((r = run_gradient(c, theta, ev))) return r;
+        // the iterations run on the high-priority stream, between two events
+        CK(cudaEventRecord(c->pev_in, c->stream));
+        CK(cudaStreamWaitEvent(c->pstream, c->pev_in, 0));
+        cudaStream_t user = c->stream;
+        c->stream = c->pstream;
+        for (int it = 0; it < n_iter && !r; ++it) {
+            cudaEvent_t *ev = it < prof ? c->events + (size_t)it * kEvents : nullptr;
+            if ((r = run_gradient(c, theta, ev))) break;
             launch_update(c, exaggeration, lr, momentum, nullptr, 1);
-            LAUNCHED("update");
-            if (ev) CK(cudaEventRecord(ev[kPhases], c->stream));
+            if (cudaGetLastError() != cudaSuccess) r = fail(c, HTS_ECUDA, "update launch failed");
+            if (!r && ev && cudaEventRecord(ev[6], c->stream) != cudaSuccess) r = fail(c, HTS_ECUDA, "event");
         }
+        c->stream = user;
+        CK(cudaEventRecord(c->pev_out, c->pstream));
+        CK(cudaStreamWaitEvent(c->stream, c->pev_out, 0));
+        if (r) return r;
     }
     c->iters += n_iter;
     int st = 0;
     if ((r = read_status(c, &st))) return r;
     for (int it = 0; it < prof; ++it) {
-        cudaEvent_t *ev = c->events + (size_t)it * (kPhases + 1);
+        cudaEvent_t *ev = c->events + (size_t)it * kEvents;
+        // keys, sort, tree, walk: consecutive main-stream marks; attract: its
+        // own interval on the side stream (overlapping); Z + update: from the
+        // join to the end of the update
+        const int from[kPhases] = {0, 1, 2, 3, 7, 5}, to[kPhases] = {1, 2, 3, 4, 8, 6};
         for (int k = 0; k < kPhases; ++k) {
+            if (k == 4 && c->nnz == 0) continue;
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            CK(cudaEventElapsedTime(&ms, ev[from[k]], ev[to[k]]));
             c->phase_ms[k] += ms;
         }
     }

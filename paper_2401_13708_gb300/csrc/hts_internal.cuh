@@ -76,6 +76,16 @@ struct TreeExport {  // optional host-visible copy of the tree (device arrays)
 struct hts_ctx {
     hts_config cfg;
     cudaStream_t stream = nullptr;
+    // side stream for the attractive sum, which needs only the point records
+    // and so overlaps the key / sort / tree / walk stages
+    cudaStream_t astream = nullptr;
+    cudaEvent_t aev_fork = nullptr, aev_join = nullptr;
+    // hts_step runs its iterations on pstream (highest priority), ordered
+    // after and before the context's stream by events; astream has the
+    // lowest priority, so attraction blocks take only SM slots that the
+    // key / sort / tree / walk kernels leave free
+    cudaStream_t pstream = nullptr;
+    cudaEvent_t pev_in = nullptr, pev_out = nullptr;
     int sm_count = 0;
     std::string err;
 
@@ -119,7 +129,7 @@ struct hts_ctx {
     int *scan_tmp = nullptr;
     int64_t scan_tmp_len = 0;
     double *red_tmp = nullptr;        // reduction partials
-    unsigned long long *minmax = nullptr;  // [0] min bits, [1] max bits
+    unsigned long long *minmax = nullptr;  // [2s] min bits, [2s+1] max bits of segment s; then the largest gamma
     double *dscal = nullptr;          // [0] Z, [1] sum p log p, [2] sum p log w, [3] sum p
     int *status = nullptr;
     unsigned long long *counters = nullptr;  // 4
@@ -154,7 +164,7 @@ struct hts_ctx {
     // instrumentation
     int64_t launches = 0;            // kernels launched since creation
     int profiling = 0;               // record phase events every iteration
-    cudaEvent_t *events = nullptr;   // kPhases + 1 per iteration slot
+    cudaEvent_t *events = nullptr;   // kPhases + 3 per iteration slot
     int event_slots = 0;
     double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int64_t phase_iters = 0;
@@ -275,23 +285,6 @@ __device__ __forceinline__ PairD pair_terms_f64(double delta)
         p.rep = p.w * r1;
     }
     return p;
-}
-
-// Double-double addition (Knuth's TwoSum followed by a fast renormalisation),
-// with explicitly rounded operations so the compiler cannot fuse or reorder.
-struct DD {
-    double hi, lo;
-};
-
-__device__ __forceinline__ DD dd_add(DD a, DD b)
-{
-    double s = __dadd_rn(a.hi, b.hi);
-    double v = __dsub_rn(s, a.hi);
-    double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, v)), __dsub_rn(b.hi, v));
-    e = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
-    double hi = __dadd_rn(s, e);
-    double lo = __dsub_rn(e, __dsub_rn(hi, s));
-    return DD{hi, lo};
 }
 
 // Quadtree level of a binary-radix-tree node from its common-prefix length

@@ -10,10 +10,16 @@
 //                 key range and split by binary search on common-prefix
 //                 lengths; equal keys are ordered by index.
 //  3. sums        exclusive prefix sums of the Einstein terms over the sorted
-//                 points, in double-double with a fixed combination order; a
-//                 cell's sums are P[hi + 1] - P[lo], accurate to ~2^-106 of the
-//                 largest prefix, so rounding them once gives the correctly
-//                 rounded float64 sums (and the oracle's midpoints).
+//                 points in 128-bit fixed point: each float64 term is scaled
+//                 by 2^E (E from the largest term and n, so no prefix can
+//                 overflow) and kept as an exact integer, the scan adds
+//                 integers (exact, any order), and a cell's sums
+//                 P[hi + 1] - P[lo] are exact; one correctly rounded
+//                 conversion gives the float64 sums the oracle rounds from its
+//                 128-bit accumulation.  Terms above 2^(52 - E) convert
+//                 exactly (E >= ~90 for 1M points within 1 - 1e-4 of the rim);
+//                 smaller ones are truncated at 2^-E.  Integer adds keep the
+//                 scan off the float64 pipe, which is narrow on this GPU.
 //  4. quad nodes  a binary node is a quadtree cell iff its quad level
 //                 floor(prefix_bits / 2) exceeds its parent's; that is the
 //                 deepest cell of a chain of one-child cells (chains collapse:
@@ -42,21 +48,30 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Sorted point records and the Einstein terms; *gmax receives the largest
+// gamma (bits of a positive double order like the double), which bounds every
+// term (|gamma v| <= gamma).
 __global__ void gather_kernel(int n, const uint32_t *__restrict__ idx, const double2 *__restrict__ y,
                               const PointF *__restrict__ pts32, const PointD *__restrict__ pts64, PointF *spts32,
-                              PointD *spts64, double *terms)
+                              PointD *spts64, double *terms, unsigned long long *gmax)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    uint32_t i = idx[p];
-    if (spts32) spts32[p] = pts32[i];
-    if (spts64) spts64[p] = pts64[i];
-    double2 q = y[i];
-    double n2 = __dadd_rn(__dmul_rn(q.x, q.x), __dmul_rn(q.y, q.y));
-    double a = __dsub_rn(1.0, n2);
-    terms[3 * p + 0] = __ddiv_rn(__dadd_rn(1.0, n2), a);
-    terms[3 * p + 1] = __ddiv_rn(__dmul_rn(2.0, q.x), a);
-    terms[3 * p + 2] = __ddiv_rn(__dmul_rn(2.0, q.y), a);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long gb = 0;
+    if (p < n) {
+        uint32_t i = idx[p];
+        if (spts32) spts32[p] = pts32[i];
+        if (spts64) spts64[p] = pts64[i];
+        double2 q = y[i];
+        double n2 = __dadd_rn(__dmul_rn(q.x, q.x), __dmul_rn(q.y, q.y));
+        double a = __dsub_rn(1.0, n2);
+        const double g = __ddiv_rn(__dadd_rn(1.0, n2), a);
+        terms[3 * p + 0] = g;
+        terms[3 * p + 1] = __ddiv_rn(__dmul_rn(2.0, q.x), a);
+        terms[3 * p + 2] = __ddiv_rn(__dmul_rn(2.0, q.y), a);
+        gb = (unsigned long long)__double_as_longlong(g);
+    }
+    for (int o = 16; o > 0; o >>= 1) gb = max(gb, __shfl_xor_sync(0xffffffffu, gb, o));
+    if ((threadIdx.x & 31) == 0 && gb) atomicMax(gmax, gb);
 }
 
 __device__ __forceinline__ int prefix_len(const uint64_t *__restrict__ keys, int n, int i, int j)
@@ -101,107 +116,148 @@ __global__ void radix_tree_kernel(int n, const uint64_t *__restrict__ keys, int 
     if (i == 0) parent[0] = -1;
 }
 
-// ---- exclusive prefix sums of the Einstein terms in double-double ----------
+// ---- exclusive prefix sums of the Einstein terms in 128-bit fixed point -----
 // P[p] = sum of terms of sorted points 0 .. p-1 (three quantities), so the
-// sums of any cell [lo, hi] are P[hi + 1] - P[lo].  Fixed block shape and
-// fixed combination order: the result is reproducible; double-double keeps
-// the absolute error near 2^-106 of the largest prefix, far below one float64
-// ulp of any cell sum, so the cell sums round as the exact sums do.
+// sums of any cell [lo, hi] are P[hi + 1] - P[lo].
 constexpr int kScanT = 256;            // threads per scan block
 constexpr int kScanI = 4;              // elements per thread
 constexpr int kScanB = kScanT * kScanI;
 
-struct DD3 {
-    DD g, x, y;
+typedef __int128 fx_t;
+
+struct FX3 {
+    fx_t g, x, y;
 };
 
-__device__ __forceinline__ DD3 dd3_add(const DD3 &a, const DD3 &b)
+__device__ __forceinline__ FX3 fx3_add(const FX3 &a, const FX3 &b) { return FX3{a.g + b.g, a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ FX3 fx3_zero() { return FX3{0, 0, 0}; }
+
+__device__ __forceinline__ fx_t fx_shfl_up(fx_t v, int o)
 {
-    return DD3{dd_add(a.g, b.g), dd_add(a.x, b.x), dd_add(a.y, b.y)};
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    const unsigned long long l2 = __shfl_up_sync(0xffffffffu, lo, o), h2 = __shfl_up_sync(0xffffffffu, hi, o);
+    return (fx_t)(((unsigned __int128)h2 << 64) | l2);
 }
 
-__device__ __forceinline__ DD3 dd3_zero() { return DD3{{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}}; }
-
-__device__ __forceinline__ DD3 dd3_shfl_up(const DD3 &v, int o)
+__device__ __forceinline__ FX3 fx3_shfl_up(const FX3 &v, int o)
 {
-    DD3 r;
-    r.g.hi = __shfl_up_sync(0xffffffffu, v.g.hi, o);
-    r.g.lo = __shfl_up_sync(0xffffffffu, v.g.lo, o);
-    r.x.hi = __shfl_up_sync(0xffffffffu, v.x.hi, o);
-    r.x.lo = __shfl_up_sync(0xffffffffu, v.x.lo, o);
-    r.y.hi = __shfl_up_sync(0xffffffffu, v.y.hi, o);
-    r.y.lo = __shfl_up_sync(0xffffffffu, v.y.lo, o);
-    return r;
+    return FX3{fx_shfl_up(v.g, o), fx_shfl_up(v.x, o), fx_shfl_up(v.y, o)};
+}
+
+// Scale exponent E with n * gmax * 2^E < 2^125: no prefix sum can overflow.
+__device__ __forceinline__ int fx_exponent(unsigned long long gmax_bits, int n)
+{
+    const int e = (int)((gmax_bits >> 52) & 0x7ff) - 1022;  // gmax >= 1 is normal: gmax < 2^e
+    const int lg = 32 - __clz(max(n, 1));                    // n < 2^lg
+    return 125 - e - lg;
+}
+
+// 2^k for -1022 <= k <= 1023 (a normal float64 built from its exponent bits).
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// x * 2^E as a 128-bit integer, rounded toward minus infinity (exact when
+// x is a multiple of 2^-E, i.e. |x| >= 2^(52 - E) or x = 0).
+__device__ __forceinline__ fx_t fx_from_double(double x, int E)
+{
+    const double hs = x * pow2(E - 64);   // |hs| < 2^61: a power-of-two scaling, exact
+    const double hf = floor(hs);
+    const double rem = hs - hf;           // exact, in [0, 1)
+    const long long hi = (long long)hf;
+    const unsigned long long lo = __double2ull_rz(rem * 18446744073709551616.0);  // rem * 2^64 < 2^64
+    return (fx_t)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+}
+
+// v * 2^-E correctly rounded to float64: the top 64 significant bits, with a
+// sticky bit for the rest, go through one round-to-nearest conversion.
+__device__ __forceinline__ double fx_to_double(fx_t v, int E)
+{
+    const bool neg = v < 0;
+    const unsigned __int128 m = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+    const unsigned long long top = (unsigned long long)(m >> 64), low = (unsigned long long)m;
+    double d;
+    if (top == 0) {
+        d = __ull2double_rn(low);
+    } else {
+        const int sh = 64 - __clzll((long long)top);  // 1 .. 64
+        const unsigned long long lowmask = sh >= 64 ? ~0ull : ((1ull << sh) - 1ull);
+        const unsigned long long t = (unsigned long long)(m >> sh) | ((low & lowmask) ? 1ull : 0ull);
+        d = __ull2double_rn(t) * pow2(sh);
+    }
+    d = d * pow2(-E);
+    return neg ? -d : d;
 }
 
 // One block scans kScanB consecutive elements: out[i] = exclusive prefix within
-// the block, tot[block] = block total.  Input: raw terms (3 doubles per point)
-// when `terms` is given, otherwise DD3 values.
-__global__ void __launch_bounds__(kScanT) dd_scan_block_kernel(int len, const double *__restrict__ terms,
-                                                              const DD3 *__restrict__ in, DD3 *out, DD3 *tot)
+// the block, tot[block] = block total.  Input: float64 terms (3 per point,
+// converted with the exponent from *gmax) when `terms` is given, otherwise
+// FX3 values.
+__global__ void __launch_bounds__(kScanT) fx_scan_block_kernel(int len, const double *__restrict__ terms,
+                                                              const unsigned long long *__restrict__ gmax, int n,
+                                                              const FX3 *__restrict__ in, FX3 *out, FX3 *tot)
 {
-    __shared__ DD3 wsum[kScanT / 32];
+    __shared__ FX3 wsum[kScanT / 32];
+    const int E = terms ? fx_exponent(*gmax, n) : 0;
     const int base = blockIdx.x * kScanB + threadIdx.x * kScanI;
-    DD3 v[kScanI];
-    DD3 t = dd3_zero();
+    FX3 v[kScanI];
+    FX3 t = fx3_zero();
 #pragma unroll
     for (int k = 0; k < kScanI; ++k) {
         const int i = base + k;
         if (i < len) {
             if (terms) {
-                v[k] = DD3{{terms[3 * i], 0.0}, {terms[3 * i + 1], 0.0}, {terms[3 * i + 2], 0.0}};
+                v[k] = FX3{fx_from_double(terms[3 * i], E), fx_from_double(terms[3 * i + 1], E),
+                           fx_from_double(terms[3 * i + 2], E)};
             } else {
                 v[k] = in[i];
             }
         } else {
-            v[k] = dd3_zero();
+            v[k] = fx3_zero();
         }
-        t = dd3_add(t, v[k]);
+        t = fx3_add(t, v[k]);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    DD3 inc = t;
+    FX3 inc = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        DD3 u = dd3_shfl_up(inc, o);
-        if (lane >= o) inc = dd3_add(u, inc);
+        FX3 u = fx3_shfl_up(inc, o);
+        if (lane >= o) inc = fx3_add(u, inc);
     }
-    DD3 excl = dd3_shfl_up(inc, 1);
-    if (lane == 0) excl = dd3_zero();
+    FX3 excl = fx3_shfl_up(inc, 1);
+    if (lane == 0) excl = fx3_zero();
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
-    DD3 woff = dd3_zero();
-    for (int k = 0; k < w; ++k) woff = dd3_add(woff, wsum[k]);
-    DD3 run = dd3_add(woff, excl);
+    FX3 run = excl;
+    for (int k = 0; k < w; ++k) run = fx3_add(run, wsum[k]);
 #pragma unroll
     for (int k = 0; k < kScanI; ++k) {
         const int i = base + k;
         if (i < len) out[i] = run;
-        run = dd3_add(run, v[k]);
+        run = fx3_add(run, v[k]);
     }
     if (threadIdx.x == kScanT - 1) tot[blockIdx.x] = run;
 }
 
-__global__ void dd_scan_add_kernel(int len, DD3 *out, const DD3 *__restrict__ off)
+__global__ void fx_scan_add_kernel(int len, FX3 *out, const FX3 *__restrict__ off)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < len) out[i] = dd3_add(off[i / kScanB], out[i]);
+    if (i < len) out[i] = fx3_add(off[i / kScanB], out[i]);
 }
 
 // Exclusive scan of len elements into out[0 .. len-1]; the grand total goes to
 // *total.  tmp holds the block totals of every recursion level.
-void dd_scan(int len, const double *terms, const DD3 *in, DD3 *out, DD3 *total, DD3 *tmp, cudaStream_t s,
-             int64_t *launches)
+void fx_scan(int len, const double *terms, const unsigned long long *gmax, int n, const FX3 *in, FX3 *out,
+             FX3 *total, FX3 *tmp, cudaStream_t s, int64_t *launches)
 {
     const int blocks = (len + kScanB - 1) / kScanB;
-    DD3 *tot = tmp;
-    dd_scan_block_kernel<<<blocks, kScanT, 0, s>>>(len, terms, in, out, tot);
+    FX3 *tot = tmp;
+    fx_scan_block_kernel<<<blocks, kScanT, 0, s>>>(len, terms, gmax, n, in, out, tot);
     *launches += 1;
     if (blocks == 1) {
-        cudaMemcpyAsync(total, tot, sizeof(DD3), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(total, tot, sizeof(FX3), cudaMemcpyDeviceToDevice, s);
         return;
     }
-    dd_scan(blocks, nullptr, tot, tot, total, tmp + blocks, s, launches);
-    dd_scan_add_kernel<<<(len + 255) / 256, 256, 0, s>>>(len, out, tot);
+    fx_scan(blocks, nullptr, nullptr, 0, tot, tot, total, tmp + blocks, s, launches);
+    fx_scan_add_kernel<<<(len + 255) / 256, 256, 0, s>>>(len, out, tot);
     *launches += 1;
 }
 
@@ -345,7 +401,8 @@ struct EmitArgs {
     const PointD *spts64;
     const int *left, *parent, *leaf_parent, *lo_arr, *hi_arr, *pref, *quad, *cnt, *pre;
     const unsigned *mask;
-    const DD3 *prefix;  // n + 1 exclusive prefix sums of the Einstein terms
+    const FX3 *prefix;  // n + 1 exclusive prefix sums of the Einstein terms (fixed point)
+    const unsigned long long *gmax;  // largest gamma (bits): the fixed-point exponent
     const unsigned long long *mm;
     NodeF *nodes32;
     NodeD *nodes64;
@@ -364,10 +421,11 @@ __global__ void emit_kernel(EmitArgs A)
         int rank = __popc(A.mask[lo] & ((1u << ell) - 1u));  // shallower cells starting at lo
         int pos = A.pre[lo] + rank;
         int skip = A.pre[hi + 1];
-        const DD3 p1 = A.prefix[hi + 1], p0 = A.prefix[lo];
-        const double sg = dd_add(p1.g, DD{-p0.g.hi, -p0.g.lo}).hi;
-        const double sux = dd_add(p1.x, DD{-p0.x.hi, -p0.x.lo}).hi;
-        const double suy = dd_add(p1.y, DD{-p0.y.hi, -p0.y.lo}).hi;
+        const FX3 p1 = A.prefix[hi + 1], p0 = A.prefix[lo];
+        const int E = fx_exponent(*A.gmax, n);
+        const double sg = fx_to_double(p1.g - p0.g, E);
+        const double sux = fx_to_double(p1.x - p0.x, E);
+        const double suy = fx_to_double(p1.y - p0.y, E);
         double mx = __ddiv_rn(sux, sg), my = __ddiv_rn(suy, sg);
         double sq = __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))));
         double cx = __ddiv_rn(mx, __dadd_rn(1.0, sq)), cy = __ddiv_rn(my, __dadd_rn(1.0, sq));
@@ -495,10 +553,12 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex)
     cudaStream_t s = c->stream;
     const bool f32 = c->cfg.precision == HTS_FP32_MIXED;
     const int gp = (n + kBlock - 1) / kBlock;
+    unsigned long long *gmax = c->minmax + 2 * kMaxSegments;
+    cudaMemsetAsync(gmax, 0, sizeof(unsigned long long), s);
     gather_kernel<<<gp, kBlock, 0, s>>>(n, c->idx, c->y, c->pts32, c->pts64, f32 ? c->spts32 : nullptr,
-                                        f32 ? nullptr : c->spts64, c->terms);
+                                        f32 ? nullptr : c->spts64, c->terms, gmax);
     c->launches += 4;  // gather, quad_mark, count, emit
-    DD3 *prefix = reinterpret_cast<DD3 *>(c->bn_sum);  // n + 1 entries
+    FX3 *prefix = reinterpret_cast<FX3 *>(c->bn_sum);  // n + 1 entries
     unsigned *mask = reinterpret_cast<unsigned *>(c->bn_flag);
     cudaMemsetAsync(mask, 0, sizeof(unsigned) * (size_t)n, s);
     if (n > 1) {
@@ -506,7 +566,8 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex)
         radix_tree_kernel<<<gi, kBlock, 0, s>>>(n, c->keys, c->bn_left, c->bn_right, c->bn_parent, c->leaf_parent,
                                                 c->bn_lo, c->bn_hi, c->bn_pref);
         c->launches += 1;
-        dd_scan(n, c->terms, nullptr, prefix, prefix + n, reinterpret_cast<DD3 *>(c->red_tmp), s, &c->launches);
+        fx_scan(n, c->terms, gmax, n, nullptr, prefix, prefix + n, reinterpret_cast<FX3 *>(c->red_tmp), s,
+                &c->launches);
         quad_mark_kernel<<<gp, kBlock, 0, s>>>(n, c->bn_parent, c->leaf_parent, c->bn_lo, c->bn_pref, c->bn_quad,
                                                mask);
     }
@@ -533,6 +594,7 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex)
     A.mask = mask;
     A.prefix = prefix;
     A.mm = c->minmax;
+    A.gmax = gmax;
     A.nodes32 = f32 ? c->nodes32 : nullptr;
     A.nodes64 = f32 ? nullptr : c->nodes64;
     A.ex = ex ? *ex : TreeExport{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
