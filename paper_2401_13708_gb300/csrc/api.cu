@@ -114,6 +114,10 @@ int ensure_points(hts_ctx *c, int64_t n)
         AL(c->spts64, N);
         AL(c->nodes64, 2 * N);
     }
+    // a node slot never written by a tree build reads as an empty bucket
+    // (count 0), which the walk steps over
+    if (c->nodes32 && cudaMemset(c->nodes32, 0, sizeof(NodeF) * 2 * N) != cudaSuccess) return HTS_ECUDA;
+    if (c->nodes64 && cudaMemset(c->nodes64, 0, sizeof(NodeD) * 2 * N) != cudaSuccess) return HTS_ECUDA;
     AL(c->keys, N);
     AL(c->keys_alt, N);
     AL(c->idx, N);
@@ -132,7 +136,7 @@ int ensure_points(hts_ctx *c, int64_t n)
     AL(c->cnt, N + 1);
     AL(c->pre, N + 1);
     const int64_t tiles = ((int64_t)N + 4095) / 4096;
-    AL(c->sort_counts, (size_t)(256 * tiles));
+    AL(c->sort_scratch, (8 * 256 + 64) / 2 + sort_status_words((int64_t)N));
     c->scan_tmp_len = scan_tmp_size(std::max<int64_t>(256 * tiles, (int64_t)N + 1));
     AL(c->scan_tmp, (size_t)c->scan_tmp_len);
     AL(c->red_tmp, std::max<size_t>(3 * ((size_t)N * 32 / 256 + 2), 512));  // also >= 6 (N / 1024 + 2)
@@ -454,7 +458,7 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->bn_left); dfree(&c->bn_right); dfree(&c->bn_parent); dfree(&c->leaf_parent);
     dfree(&c->bn_lo); dfree(&c->bn_hi); dfree(&c->bn_pref); dfree(&c->bn_flag); dfree(&c->bn_quad);
     dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
-    dfree(&c->sort_counts); dfree(&c->scan_tmp); dfree(&c->red_tmp); dfree(&c->minmax);
+    dfree(&c->sort_scratch); dfree(&c->scan_tmp); dfree(&c->red_tmp); dfree(&c->minmax);
     dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq);
     dfree(&c->seg_off); dfree(&c->seg_of); dfree(&c->seg_lr); dfree(&c->seg_z);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);

@@ -125,7 +125,7 @@ struct hts_ctx {
     hts::NodeD *nodes64 = nullptr;
 
     // scratch
-    uint32_t *sort_counts = nullptr;  // 256 * tiles
+    unsigned long long *sort_scratch = nullptr;  // digit offsets, tile counters, look-back status words
     int *scan_tmp = nullptr;
     int64_t scan_tmp_len = 0;
     double *red_tmp = nullptr;        // reduction partials
@@ -180,6 +180,7 @@ void launch_make_keys(hts_ctx *c);
 void launch_sort_pairs(hts_ctx *c);
 int scan_exclusive(const int *in, int *out, int64_t len, int *tmp, cudaStream_t s);  // returns kernels launched
 int64_t scan_tmp_size(int64_t len);
+size_t sort_status_words(int64_t n);
 // tree.cu
 void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex);
 // traverse.cu

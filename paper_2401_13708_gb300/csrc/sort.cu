@@ -2,16 +2,25 @@
 //
 // The tree of Sec. 4.1 is a hierarchy over the keys, so sorting the points
 // by key puts every cell's points in one contiguous run.  Eight stable
-// passes of 8 bits each (keys use the low 58 bits).  Per pass:
-//   hist     one 4096-key tile per block: 256-bin shared histogram,
-//            written digit-major as counts[digit][tile];
-//   scan     exclusive scan of the counts gives every (digit, tile) its
-//            first output slot;
-//   scatter  each warp owns 512 consecutive keys of the tile; warp
-//            histograms (match_any + popc), a per-digit prefix over the 8
-//            warps, then a second in-order pass ranks each key among equal
-//            digits (match_any + popc of lower lanes) and writes it out.
-// Traffic per pass: 8 B/key read (hist) + 12 B read + 12 B write (scatter).
+// passes of 8 bits each (58 key bits + 6 segment bits), one kernel per pass:
+//   digit_hist  once per sort: the global histograms of all eight digits
+//               (they do not depend on the order of the keys), then an
+//               exclusive scan of each gives every digit its first slot;
+//   onesweep    per pass, one 4096-key tile per block, tiles taken in launch
+//               order from an atomic counter: warp histograms (match_any +
+//               popc), the tile's per-digit counts published to a status
+//               word, and a decoupled look-back over earlier tiles (thread d
+//               for digit d) adds up the keys of digit d before this tile;
+//               then each key is ranked among equal digits in order and
+//               written out.  Look-back spins are bounded: a timeout sets a
+//               status bit (reported as an error), and out-of-range
+//               positions are never written.
+// Traffic per pass: 12 B read + 12 B write per key (+ 8 B read once for the
+// histograms).
+#include <cuda/atomic>
+
+#include <algorithm>
+
 #include "hts_internal.cuh"
 
 namespace hts {
@@ -26,34 +35,82 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 
-__global__ void __launch_bounds__(kSortThreads) hist_kernel(const uint64_t *__restrict__ keys, int n, int shift,
-                                                            int tiles, int *counts)
+constexpr int kPasses = 8;
+constexpr unsigned long long kFlagAgg = 1ull << 62;   // tile count published
+constexpr unsigned long long kFlagPre = 2ull << 62;   // inclusive prefix published
+constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
+constexpr int kSpinLimit = 1 << 22;
+
+// Global histograms of all eight digits; hist[pass][digit] (2048 ints).
+__global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint64_t *__restrict__ keys, int n,
+                                                                  int *hist)
 {
-    __shared__ int h[256];
-    h[threadIdx.x] = 0;
+    __shared__ int h[kPasses][256];
+    for (int k = threadIdx.x; k < kPasses * 256; k += kSortThreads) (&h[0][0])[k] = 0;
     __syncthreads();
-    int base = blockIdx.x * kTile;
-#pragma unroll 4
-    for (int k = threadIdx.x; k < kTile; k += kSortThreads) {
-        int i = base + k;
-        if (i < n) atomicAdd(&h[(int)((keys[i] >> shift) & 0xFFu)], 1);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int base = blockIdx.x * kTile;
+    for (int r = 0; r < kTile / kSortThreads; ++r) {
+        const int i = base + r * kSortThreads + threadIdx.x;
+        const bool ok = i < n;
+        const uint64_t key = ok ? keys[i] : 0ull;
+#pragma unroll
+        for (int p = 0; p < kPasses; ++p) {
+            const int d = ok ? (int)((key >> (8 * p)) & 0xFFu) : 256 + lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (ok && (peers & lt) == 0u) atomicAdd(&h[p][d], __popc(peers));
+        }
     }
     __syncthreads();
-    counts[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+    for (int k = threadIdx.x; k < kPasses * 256; k += kSortThreads) {
+        const int v = (&h[0][0])[k];
+        if (v) atomicAdd(&hist[k], v);
+    }
 }
 
-__global__ void __launch_bounds__(kSortThreads) scatter_kernel(const uint64_t *__restrict__ kin,
-                                                               const uint32_t *__restrict__ vin,
-                                                               uint64_t *__restrict__ kout,
-                                                               uint32_t *__restrict__ vout, int n, int shift,
-                                                               int tiles, const int *__restrict__ offsets)
+// hist[pass][digit] -> exclusive prefix over digits (in place), one warp per pass.
+__global__ void digit_offsets_kernel(int *hist)
+{
+    const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (p >= kPasses) return;
+    int *h = hist + p * 256;
+    int v[8], local = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[k] = h[lane * 8 + k];
+        local += v[k];
+    }
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int run = incl - local;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        h[lane * 8 + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *__restrict__ kin,
+                                                                const uint32_t *__restrict__ vin,
+                                                                uint64_t *__restrict__ kout,
+                                                                uint32_t *__restrict__ vout, int n, int shift,
+                                                                const int *__restrict__ digit_off,
+                                                                unsigned long long *tile_status, int *tile_ctr,
+                                                                int *status)
 {
     __shared__ int wh[kWarps][256];
+    __shared__ int s_tile;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1);  // tiles in launch order
     __syncthreads();
+    const int tile = s_tile;
 
-    const int base = blockIdx.x * kTile + w * kPerWarp;
+    const int base = tile * kTile + w * kPerWarp;
     const unsigned lt = (1u << lane) - 1u;
     uint64_t key[kRounds];
     uint32_t val[kRounds];
@@ -71,14 +128,43 @@ __global__ void __launch_bounds__(kSortThreads) scatter_kernel(const uint64_t *_
     }
     __syncthreads();
     {
-        int d = threadIdx.x;  // 256 threads = 256 digits
-        int run = offsets[d * tiles + blockIdx.x];
+        const int d = threadIdx.x;  // 256 threads = 256 digits
+        int cnt = 0;
 #pragma unroll
         for (int k = 0; k < kWarps; ++k) {
-            int t = wh[k][d];
-            wh[k][d] = run;
-            run += t;
+            const int t = wh[k][d];
+            wh[k][d] = cnt;  // exclusive prefix over the warps of this tile
+            cnt += t;
         }
+        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> mine(tile_status[(size_t)tile * 256 + d]);
+        long long excl = 0;
+        if (tile == 0) {
+            mine.store(kFlagPre | (unsigned long long)cnt, cuda::memory_order_relaxed);
+        } else {
+            mine.store(kFlagAgg | (unsigned long long)cnt, cuda::memory_order_relaxed);
+            // decoupled look-back: add tile counts until an inclusive prefix
+            for (int t = tile - 1; t >= 0; --t) {
+                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> other(
+                    tile_status[(size_t)t * 256 + d]);
+                unsigned long long v = other.load(cuda::memory_order_relaxed);
+                int spins = 0;
+                while ((v >> 62) == 0ull && ++spins < kSpinLimit) {
+                    __nanosleep(64);
+                    v = other.load(cuda::memory_order_relaxed);
+                }
+                if ((v >> 62) == 0ull) {  // gave up: report, and leave positions invalid
+                    atomicOr(status, 4);
+                    excl = (long long)n;
+                    break;
+                }
+                excl += (long long)(v & kValMask);
+                if ((v & kFlagPre) && !(v & kFlagAgg)) break;
+            }
+            mine.store(kFlagPre | (unsigned long long)(excl + cnt), cuda::memory_order_relaxed);
+        }
+        const int off = digit_off[d] + (int)min(excl, (long long)n);
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) wh[k][d] += off;
     }
     __syncthreads();
 #pragma unroll
@@ -92,8 +178,12 @@ __global__ void __launch_bounds__(kSortThreads) scatter_kernel(const uint64_t *_
         if (ok && (peers & lt) == 0u) wh[w][dig[r]] += __popc(peers);
         __syncwarp();
         if (ok) {
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            if (pos >= 0 && pos < n) {
+                kout[pos] = key[r];
+                vout[pos] = val[r];
+            } else {
+                atomicOr(status, 4);
+            }
         }
     }
 }
@@ -176,17 +266,30 @@ int scan_exclusive(const int *in, int *out, int64_t len, int *tmp, cudaStream_t 
     return k + 2;
 }
 
+size_t sort_status_words(int64_t n)
+{
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    return (size_t)kPasses * 256 * (size_t)std::max<int64_t>(tiles, 1);
+}
+
 void launch_sort_pairs(hts_ctx *c)
 {
-    int n = (int)c->n;
-    int tiles = (n + kTile - 1) / kTile;
-    int *counts = (int *)c->sort_counts;
+    const int n = (int)c->n;
+    const int tiles = (n + kTile - 1) / kTile;
+    // scratch: 2048 ints of digit offsets, 8 tile counters, then the status words
+    int *hist = reinterpret_cast<int *>(c->sort_scratch);
+    int *ctr = hist + kPasses * 256;
+    unsigned long long *stat = reinterpret_cast<unsigned long long *>(c->sort_scratch + (kPasses * 256 + 64) / 2);
+    cudaMemsetAsync(c->sort_scratch, 0, sizeof(unsigned long long) * ((kPasses * 256 + 64) / 2 +
+                                                                      (size_t)kPasses * 256 * tiles), c->stream);
+    digit_hist_kernel<<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
+    digit_offsets_kernel<<<1, 32 * kPasses, 0, c->stream>>>(hist);
+    c->launches += 2 + kPasses;
     uint64_t *ka = c->keys, *kb = c->keys_alt;
     uint32_t *va = c->idx, *vb = c->idx_alt;
-    for (int shift = 0; shift < 64; shift += 8) {
-        hist_kernel<<<tiles, kSortThreads, 0, c->stream>>>(ka, n, shift, tiles, counts);
-        c->launches += 2 + scan_exclusive(counts, counts, (int64_t)256 * tiles, c->scan_tmp, c->stream);
-        scatter_kernel<<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, shift, tiles, counts);
+    for (int p = 0; p < kPasses; ++p) {
+        onesweep_kernel<<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
+                                                               stat + (size_t)p * 256 * tiles, ctr + p, c->status);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }

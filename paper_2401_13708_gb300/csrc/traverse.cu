@@ -144,7 +144,9 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
             }
         }
         if (COUNT && lane == 0) ++c_visit;
-        node = max(next, node + 1);  // always advances: the loop ends within m visits
+        // next > node always: a cell's skip exceeds its position (emit writes
+        // no cell otherwise) and unwritten slots are zero (empty buckets)
+        node = next;
     }
     if (valid) {
         const uint32_t i = idx[p];
@@ -256,7 +258,7 @@ __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__r
             }
         }
         if (COUNT && lane == 0) ++c_visit;
-        node = max(next, node + 1);
+        node = next;  // as in the float32 walk
     }
     if (valid) {
         const uint32_t i = idx[p];

@@ -107,8 +107,9 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
     if (A.g_out) A.g_out[i] = make_double2(gx, gy);
     if (!A.do_step) return;
     double2 v = A.vel[i];
-    const double lam = 2.0 / (1.0 - n2);
-    const double sc = A.metric_pow == 2 ? 1.0 / (lam * lam) : 1.0 / lam;
+    const double a = 1.0 - n2;  // 2 / lambda (Eq. PoincareMetric)
+    const double hl = 0.5 * a;  // 1 / lambda
+    const double sc = A.metric_pow == 2 ? hl * hl : hl;
     double kx = 1.0, ky = 1.0;
     if (A.use_gains) {
         double2 gn = A.gains[i];
@@ -126,15 +127,15 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
     const double nv = sqrt(v.x * v.x + v.y * v.y);
     double2 q = p;
     if (nv > 0.0) {
-        const double t = tanh(lam * nv / 2.0);
-        const double ux = t * v.x / nv, uy = t * v.y / nv;
+        // exp map: p (+) tanh(lambda |v| / 2) v / |v|, lambda |v| / 2 = |v| / a
+        const double f = tanh(nv / a) / nv;
+        const double ux = f * v.x, uy = f * v.y;
         const double pu = p.x * ux + p.y * uy;
         const double nu = ux * ux + uy * uy;
         const double ca = 1.0 + 2.0 * pu + nu;
-        const double cb = 1.0 - n2;
-        const double den = 1.0 + 2.0 * pu + n2 * nu;
-        q.x = (ca * p.x + cb * ux) / den;
-        q.y = (ca * p.y + cb * uy) / den;
+        const double rden = 1.0 / (1.0 + 2.0 * pu + n2 * nu);
+        q.x = (ca * p.x + a * ux) * rden;
+        q.y = (ca * p.y + a * uy) * rden;
     }
     const double r = sqrt(q.x * q.x + q.y * q.y);
     if (r >= 1.0 - A.eps / 2.0) {
