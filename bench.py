@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cache", default="", help="directory to keep the generated workload in (reused if present)")
     ap.add_argument("--shapes", default="",
                     help="walk threads per block,attraction lanes per row (e.g. 256,8) instead of the autotuner")
+    ap.add_argument("--suite", action="store_true",
+                    help="per-workload report (all five configurations) instead of the headline line")
     ap.add_argument("--profile-only", action="store_true",
                     help="FP32-mixed steps only (for a profiler): no FP64 arm, e2e or oracle")
     return ap.parse_args()
@@ -244,6 +246,38 @@ def _cuda():
 FLOPS_CRITERION = 12
 FLOPS_PAIR = 21
 
+# Algorithmic DRAM bytes of the memory-bound phases (per point unless noted):
+#   keys    Y 16 read + point record 32 + radial 8 written, radial 8 read +
+#           key/index 12 written                                        -> 76
+#   sort    keys read once for the digit histograms (8) + 8 passes x
+#           (12 read + 12 written)                                      -> 200
+#   tree    gather 108 (index, Y, record in; sorted record, terms out),
+#           radix tree 52, fixed-point scan 168, marks/counts/scan 20,
+#           emit 144 (prefix sums in, 32-byte node out)                  -> ~490
+#   attract 8 per non-zero (index + value) + 24 per row (indptr, force)
+#           (the 32-byte neighbour records are gathered from L2)
+#   update  Y, velocity, both forces 64 read + Z 8 + Y, velocity 32 written -> 104
+BYTES_PER_POINT = {"keys": 76, "sort": 200, "tree": 490, "update": 104}
+ATTRACT_BYTES_PER_NNZ, ATTRACT_BYTES_PER_ROW = 8, 24
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu or /proc/cpuinfo), for the oracle timing."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
 
 EARLY_ITERS = 250  # Sec. 5.2.1: 250 early-exaggeration iterations, then at most 750 plain ones
 
@@ -356,9 +390,43 @@ def run_ours(args, rank, world, local):
     traffic = None  # DRAM bytes per walk launch from the committed ncu capture, scaled to n
     tf = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     if os.path.exists(tf):
+        import hashlib
         rec = json.load(open(tf))
-        if rec.get("kernel") == "walk_f32_kernel" and rec.get("dram_bytes_per_launch"):
+        src = os.path.join(ROOT, "paper_2401_13708_gb300", "csrc", "traverse.cu")
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        # only counters taken on the kernel as it is now
+        if (rec.get("kernel") == "walk_f32_kernel" and rec.get("dram_bytes_per_launch")
+                and rec.get("traverse_cu_sha256") == sha):
             traffic = rec["dram_bytes_per_launch"] * n / rec["captured_n"]
+
+    # ---- per-kernel rooflines: the timed segment replayed with every phase
+    # timed alone (the attraction on the main stream instead of overlapped)
+    t.set_Y(y_s)
+    t.set_state(v_s, None, 0)
+    t.set_profiling(True, serial=True)
+    t.get_profile()
+    protocol(t, W, K, theta, lr)
+    sprof, siters = t.get_profile()
+    t.set_profiling(False)
+    sphase = {k: v / max(siters, 1) for k, v in sprof.items()}
+    from paper_2401_13708_gb300 import measure_peaks
+    mpeaks = measure_peaks(local)
+    hbm = peaks.get("hbm_gbs")
+    kernels = {}
+    for ph, bpp in BYTES_PER_POINT.items():
+        gbs = bpp * n / (sphase[ph] * 1e-3) / 1e9
+        kernels[ph] = {"bound": "hbm", "ms": sphase[ph], "algorithmic_bytes": bpp * n, "achieved": gbs,
+                       "unit": "GB/s", "peak": hbm, "frac": gbs / hbm if hbm else None}
+    abytes = ATTRACT_BYTES_PER_NNZ * int(w.nnz) + ATTRACT_BYTES_PER_ROW * n
+    agbs = abytes / (sphase["attract"] * 1e-3) / 1e9
+    kernels["attract"] = {"bound": "hbm", "ms": sphase["attract"], "algorithmic_bytes": abytes, "achieved": agbs,
+                          "unit": "GB/s", "peak": hbm, "frac": agbs / hbm if hbm else None,
+                          "note": "runs overlapped with the walk in the timed iteration"}
+    wflop = flops / (sphase["walk"] * 1e-3) / 1e12
+    kernels["walk"] = {"bound": "alu", "ms": sphase["walk"], "achieved": wflop, "unit": "TFLOP/s",
+                       "peak": fp32_peak, "frac": wflop / fp32_peak,
+                       "frac_of_measured_fp32": wflop / mpeaks["fp32_fma_tflops"]
+                       if mpeaks["fp32_fma_tflops"] else None}
 
     # ---- end to end through the C ABI, all iteration state in host memory -
     k_e2e = K  # the same iterations as the device-timed segment
@@ -410,9 +478,28 @@ def run_ours(args, rank, world, local):
                           "z_rel_err": float(abs(z - ref["Z"]) / ref["Z"])}
             if name == "y0":
                 cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": cores, "kind": "oracle",
+                       "cpu_model": cpu_model(),
                        "sample": (f"one FP64 oracle pass at N={n} on Y0: literal-insertion tree, BH walks of all "
                                   f"{n} points (for Z) and gradient rows for {len(rows)} sampled points; "
                                   f"{t_or:.1f} s")}
+        # one thread: the tree once and a bounded sample of row walks, extrapolated
+        import oracle
+        all_cores = oracle.set_threads(0)
+        oracle.set_threads(1)
+        t0 = time.time()
+        tree = oracle.PreparedTree(y0)
+        t_tree = time.time() - t0
+        srows = rng.choice(n, size=min(4000, n), replace=False)
+        t0 = time.time()
+        tree.walk_rows(srows, w.indptr, w.indices, np.asarray(w.values, dtype=np.float64), theta, 1.0, 1.0)
+        t_rows = time.time() - t0
+        tree.close()
+        oracle.set_threads(all_cores)
+        t1 = t_tree + t_rows * n / len(srows)
+        if cpu is not None:
+            cpu["single_thread"] = {"value": 1.0 / t1, "unit": UNIT, "cores": 1,
+                                    "sample": (f"tree built once ({t_tree:.2f} s) + {len(srows)} row walks "
+                                               f"({t_rows:.2f} s) at Y0, extrapolated to {n} rows")}
 
     if rank != 0:
         return
@@ -442,10 +529,16 @@ def run_ours(args, rank, world, local):
                                    "replay_reproduced_trajectory": replay_same},
         "roofline": {"kernel": "walk_f32_kernel (BH tree walk)", "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "frac_of_measured_fp32": achieved / mpeaks["fp32_fma_tflops"]
+                     if mpeaks["fp32_fma_tflops"] else None,
                      "dominant_phase": dominant, "walk_ms": walk_ms,
                      "peak_basis": "FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (sampled SM clock)" % (
                          props.multi_processor_count, sm_mhz)},
         "cpu_baseline": cpu,
+        "kernel_rooflines": {"source": "the timed segment replayed with each phase timed alone (CUDA events)",
+                             "hbm_peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy, read + write)",
+                             "phase_ms_per_step": sphase, "kernels": kernels},
+        "measured_peaks": dict(mpeaks, note="this library's microbenchmarks (hts_measure_peaks), this run"),
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
@@ -454,11 +547,135 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# per-configuration report (--suite): all five workloads, fixed iteration counts
+# ---------------------------------------------------------------------------
+
+def run_suite(args, rank, world, local):
+    """One JSON line per (workload, path): iterations/s and wall time to the
+    workload's fixed iteration count on one GPU (CUDA events around the
+    hts_step calls, after 3 warm-up iterations from the same start), and the
+    oracle's time per iteration on this host's cores.  FP64 runs longer than
+    ~30 s are timed on a prefix of the schedule and extrapolated (labelled)."""
+    if rank != 0:
+        return
+    import torch
+
+    import oracle
+    from paper_2401_13708_gb300 import HyperbolicTSNE, inputs
+    cores = oracle.set_threads(0)
+    model = cpu_model()
+    dev = f"cuda:{local}"
+
+    def schedule(n_total, ee, exag, mom1, mom2, lr):
+        return [(ee, exag, lr, mom1), (n_total - ee, 1.0, lr, mom2)]
+
+    def gpu_time(prec, w, y0, sched, theta, max_iters=None, segments=None, lr_scale=None, graphs=False):
+        t = HyperbolicTSNE(precision=prec, device=local)
+        t.set_P(w.indptr, w.indices, w.values)
+        t.set_Y(y0)
+        if segments is not None:
+            t.set_segments(segments, lr_scale)
+        shapes = t.autotune(theta, 2) if theta > 0 else None
+        t.set_graphs(graphs)
+        t.step(3, theta, sched[0][1], sched[0][2], sched[0][3])  # warm-up (and capture), then restart
+        t.set_Y(y0)
+        total = sum(s[0] for s in sched)
+        run = total if max_iters is None else min(total, max_iters)
+        left, todo = run, []
+        for k, ex, lr, mom in sched:
+            m = min(k, left)
+            if m > 0:
+                todo.append((m, ex, lr, mom))
+            left -= m
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for m, ex, lr, mom in todo:
+            t.step(m, theta, ex, lr, mom)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t.close()
+        out = {"iters_per_s": run / (ms / 1e3), "timed_iters": run, "schedule_iters": total,
+               "wall_s_to_schedule": ms / 1e3 * total / run, "extrapolated": run < total}
+        if shapes:
+            out["launch_shapes"] = list(shapes)
+        return out
+
+    def emit(line):
+        line.update({"data": "synthetic", "n_gpus": 1, "unit": "iters/s"})
+        print(json.dumps(line), flush=True)
+
+    def oracle_iters(w, y0, k, theta, exag, lr, mom, nseg_slices=None):
+        t0 = time.time()
+        if nseg_slices is None:
+            oracle.step(y0, np.zeros_like(y0), w.indptr, w.indices, w.values, k, theta, exag, lr, mom)
+        else:
+            for (a, b, ip, ix, vv, lr_s) in nseg_slices:
+                oracle.step(y0[a:b], np.zeros_like(y0[a:b]), ip, ix, vv, k, theta, exag, lr_s, mom)
+        dt = (time.time() - t0) / k
+        return {"s_per_iter": dt, "iters_per_s": 1.0 / dt, "iters_timed": k, "cores": cores, "cpu_model": model}
+
+    # config 1: N = 2000, FP64 CSR; 100 iterations, exaggeration 12 for 25, lr 1, momentum 0.5
+    w = inputs.make_config(1, seed=args.seed, device=dev)
+    sched = schedule(100, 25, 12.0, 0.5, 0.5, 1.0)
+    for theta in (0.0, 0.5):
+        line = {"workload": inputs.CONFIG_NAMES[1], "n": w.n, "nnz": w.nnz, "theta": theta,
+                "iterations": 100, "schedule": "25 x (exaggeration 12) + 75 x 1, lr 1, momentum 0.5"}
+        line["fp64_gpu"] = gpu_time("fp64", w, w.y0, sched, theta, graphs=True)
+        line["fp32_mixed_gpu"] = gpu_time("fp32", w, w.y0, sched, theta, graphs=True)
+        line["oracle"] = oracle_iters(w, w.y0, 100, theta, 12.0, 1.0, 0.5)
+        emit(line)
+
+    # configs 2, 3, 5: the paper's protocol, 1000 iterations, lr = N / 12000
+    for cfg, thetas in ((2, (0.5,)), (3, (0.2, 0.5, 0.8)), (5, (0.5, 0.8))):
+        w = inputs.make_config(cfg, seed=args.seed, device=dev)
+        lr = w.n / 12000.0
+        sched = schedule(1000, 250, 12.0, 0.5, 0.8, lr)
+        for theta in thetas:
+            line = {"workload": inputs.CONFIG_NAMES[cfg], "n": w.n, "nnz": w.nnz, "theta": theta,
+                    "iterations": 1000,
+                    "schedule": "250 x (exaggeration 12, momentum 0.5) + 750 x (1, 0.8), lr = N/12000"}
+            line["fp32_mixed_gpu"] = gpu_time("fp32", w, w.y0, sched, theta)
+            f64 = gpu_time("fp64", w, w.y0, sched, theta, max_iters=60 if cfg == 5 else 250)
+            line["fp64_gpu"] = f64
+            f32p = gpu_time("fp32", w, w.y0, sched, theta, max_iters=f64["timed_iters"])
+            line["fp32_mixed_speedup_over_fp64"] = {"iters": f64["timed_iters"],
+                                                    "speedup": f32p["iters_per_s"] / f64["iters_per_s"]}
+            if theta == 0.5:
+                k = 1 if cfg == 5 else 10
+                line["oracle"] = oracle_iters(w, w.y0, k, theta, 12.0, lr, 0.5)
+            emit(line)
+
+    # config 4: 64 embeddings in one context, 500 iterations (125 exaggerated), lr = n_s / 12000
+    w = inputs.make_batched(64, seed=args.seed, device=dev)
+    off = w.extra["offsets"]
+    sizes = np.diff(off).astype(np.float64)
+    sched = schedule(500, 125, 12.0, 0.5, 0.8, 1.0)
+    line = {"workload": "64 batched mixtures N~logU(500,20000), D=50, 3-20 components, perplexity {10,30,50}",
+            "n": w.n, "nnz": w.nnz, "theta": 0.5, "iterations": 500,
+            "schedule": "125 x (exaggeration 12, momentum 0.5) + 375 x (1, 0.8), lr = n_s/12000 per embedding"}
+    line["fp32_mixed_gpu_graphs"] = gpu_time("fp32", w, w.y0, sched, 0.5, segments=off, lr_scale=sizes / 12000.0,
+                                             graphs=True)
+    line["fp32_mixed_gpu_eager"] = gpu_time("fp32", w, w.y0, sched, 0.5, segments=off, lr_scale=sizes / 12000.0)
+    slices = []
+    for sg in range(len(off) - 1):
+        a, b = int(off[sg]), int(off[sg + 1])
+        e0, e1 = int(w.indptr[a]), int(w.indptr[b])
+        slices.append((a, b, (w.indptr[a:b + 1] - e0).astype(np.int64), (w.indices[e0:e1] - a).astype(np.int32),
+                       np.asarray(w.values[e0:e1], dtype=np.float64), sizes[sg] / 12000.0))
+    line["oracle"] = oracle_iters(w, w.y0, 1, 0.5, 12.0, None, 0.5, nseg_slices=slices)
+    emit(line)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.suite:
+        run_suite(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

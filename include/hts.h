@@ -190,12 +190,16 @@ HTS_API int hts_get_tree(hts_ctx *ctx, int64_t cap, int64_t *count_out, int32_t 
 HTS_API int hts_get_counters(hts_ctx *ctx, int64_t *out5);
 HTS_API int hts_set_counters(hts_ctx *ctx, int enable);
 
-/* Per-phase timing.  While profiling is on, hts_step records CUDA events on
- * the context's stream at the phase boundaries of every iteration (up to
- * 4096 per call).  hts_get_profile returns the accumulated milliseconds of
- * the six phases -- keys, sort, tree build, tree walk (or exact kernel),
- * attractive sum, Z + update -- and the number of iterations they cover,
- * then resets them.  ms6: host double[6]. */
+/* Per-phase timing.  While profiling is on, hts_step records CUDA events at
+ * the phase boundaries of every iteration (up to 4096 per call).
+ * hts_get_profile returns the accumulated milliseconds of the six phases --
+ * keys, sort, tree build, tree walk (or exact kernel), attractive sum, Z +
+ * update -- and the number of iterations they cover, then resets them.
+ * enable = 1 times the iteration as it normally runs (the attractive sum
+ * overlapped on its side stream, so its interval spans the stages it shares
+ * the GPU with); enable = 2 runs the attractive sum on the main stream
+ * between the walk and the Z reduction, so that each phase is timed alone.
+ * ms6: host double[6]. */
 HTS_API int hts_set_profiling(hts_ctx *ctx, int enable);
 HTS_API int hts_get_profile(hts_ctx *ctx, double *ms6, int64_t *iters);
 
@@ -270,6 +274,15 @@ HTS_API int hts_set_graphs(hts_ctx *ctx, int enable);
 HTS_API int hts_autotune(hts_ctx *ctx, double theta, int reps, int *tuning);
 HTS_API int hts_set_tuning(hts_ctx *ctx, int walk_block, int attract_lanes);
 HTS_API int hts_get_tuning(const hts_ctx *ctx, int *tuning);
+
+/* ---- roofline denominators ---------------------------------------------------
+ * (No counterpart in the paper.)  Measures, on `device`, the sustained issue
+ * rates that bound the hot path: out3[0] float32 FMA (TFLOP/s, 2 flop per
+ * FMA), out3[1] special-function reciprocal square roots (Tops/s), out3[2]
+ * float64 FMA (TFLOP/s).  Each is one ~5-10 ms kernel of independent chains
+ * over 64 warps per SM.  Allocates 4 bytes of device memory for the duration.
+ * Errors: HTS_EINVAL, HTS_ECUDA, HTS_EOOM. */
+HTS_API int hts_measure_peaks(int device, double *out3);
 
 /* Number of points n and non-zeros nnz currently set (either may be NULL). */
 HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);

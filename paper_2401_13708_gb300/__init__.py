@@ -6,7 +6,7 @@ seeded synthetic workloads.  Importing the package does not load the
 library; constructing a HyperbolicTSNE does, and raises if it is missing.
 """
 from .api import (EQUAL_AREA, EQUAL_LENGTH, EXACT_KL, FP32_MIXED, FP64, PAPER_EQ, HtsError,  # noqa: F401
-                  HyperbolicTSNE)
+                  HyperbolicTSNE, measure_peaks)
 
 
 def build(force: bool = False) -> str:

@@ -235,8 +235,11 @@ class HyperbolicTSNE:
         self._check(self._lib.hts_get_counters(self._ctx, out.ctypes.data_as(C.c_void_p)))
         return out
 
-    def set_profiling(self, enable: bool = True):
-        self._check(self._lib.hts_set_profiling(self._ctx, int(bool(enable))))
+    def set_profiling(self, enable: bool = True, serial: bool = False):
+        """Per-phase CUDA-event timing; serial=True runs the attractive sum on
+        the main stream so that every phase is timed alone."""
+        mode = 0 if not enable else (2 if serial else 1)
+        self._check(self._lib.hts_set_profiling(self._ctx, mode))
 
     PHASES = ("keys", "sort", "tree", "walk", "attract", "update")
 
@@ -281,5 +284,16 @@ class HyperbolicTSNE:
         return int(n.value), int(nnz.value)
 
 
-__all__ = ["HyperbolicTSNE", "HtsError", "FP64", "FP32_MIXED", "EQUAL_LENGTH", "EQUAL_AREA", "EXACT_KL", "PAPER_EQ",
+def measure_peaks(device: int = 0):
+    """Measured issue rates of this GPU: float32 FMA TFLOP/s, special-function
+    rsqrt Tops/s, float64 FMA TFLOP/s (roofline denominators)."""
+    lib = load()
+    out = np.zeros(3)
+    code = lib.hts_measure_peaks(int(device), out.ctypes.data_as(C.c_void_p))
+    if code != 0:
+        raise HtsError(code, "hts_measure_peaks failed")
+    return {"fp32_fma_tflops": float(out[0]), "mufu_rsqrt_tops": float(out[1]), "fp64_fma_tflops": float(out[2])}
+
+
+__all__ = ["HyperbolicTSNE", "measure_peaks", "HtsError", "FP64", "FP32_MIXED", "EQUAL_LENGTH", "EQUAL_AREA", "EXACT_KL", "PAPER_EQ",
            "_lib"]

@@ -25,7 +25,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
 
 # float32 kernels: flush denormals so rsqrt / log2 / rcp are single
 # special-function operations (values below 1e-30 are clamped anyway)
-PER_FILE = {"traverse.cu": ["-ftz=true"], "attract.cu": ["-ftz=true"]}
+PER_FILE = {"traverse.cu": ["-ftz=true"], "attract.cu": ["-ftz=true"], "peaks.cu": ["-ftz=true"]}
 
 
 def _sources():

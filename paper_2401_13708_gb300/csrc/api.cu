@@ -179,7 +179,8 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
 {
 #define MARK(k) \
     if (ev) CK(cudaEventRecord(ev[k], c->stream))
-    const bool attract = c->nnz > 0;
+    const bool serial = c->profiling == 2;  // every phase alone (timing)
+    const bool attract = c->nnz > 0 && !serial;
     // fork: the side stream waits for the point records (and for the stages
     // before kAttractAfter, so that it does not hold SMs they need)
     auto fork_attract = [&]() -> int {
@@ -199,7 +200,7 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
     MARK(0);
     launch_prep_points(c);
     LAUNCHED("prep_points");
-    if (!attract) CK(cudaMemsetAsync(c->fattr, 0, sizeof(double2) * (size_t)c->n, c->stream));
+    if (c->nnz == 0) CK(cudaMemsetAsync(c->fattr, 0, sizeof(double2) * (size_t)c->n, c->stream));
     if (theta == 0.0) {
         if (attract && (r = fork_attract())) return r;
         MARK(1);
@@ -226,6 +227,12 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
     }
     MARK(4);
     if (attract) CK(cudaStreamWaitEvent(c->stream, c->aev_join, 0));  // join
+    if (serial && c->nnz > 0) {
+        if (ev) CK(cudaEventRecord(ev[7], c->stream));
+        launch_attract(c);
+        LAUNCHED("attract");
+        if (ev) CK(cudaEventRecord(ev[8], c->stream));
+    }
     MARK(5);
     launch_reduce_z(c);
     LAUNCHED("reduce_z");
@@ -872,7 +879,8 @@ int hts_get_counters(hts_ctx *c, int64_t *out5)
 int hts_set_profiling(hts_ctx *c, int enable)
 {
     if (!c) return HTS_EINVAL;
-    c->profiling = enable ? 1 : 0;
+    if (enable < 0 || enable > 2) return fail(c, HTS_EINVAL, "hts_set_profiling: enable is 0, 1 or 2");
+    c->profiling = enable;
     return HTS_OK;
 }
 
