@@ -54,6 +54,7 @@ def parse():
                     help="walk threads per block,attraction lanes per row (e.g. 256,8) instead of the autotuner")
     ap.add_argument("--suite", action="store_true",
                     help="per-workload report (all five configurations) instead of the headline line")
+    ap.add_argument("--configs", default="1,2,3,4,5", help="workloads of the --suite report")
     ap.add_argument("--profile-only", action="store_true",
                     help="FP32-mixed steps only (for a profiler): no FP64 arm, e2e or oracle")
     return ap.parse_args()
@@ -617,10 +618,12 @@ def run_suite(args, rank, world, local):
         dt = (time.time() - t0) / k
         return {"s_per_iter": dt, "iters_per_s": 1.0 / dt, "iters_timed": k, "cores": cores, "cpu_model": model}
 
+    want = {int(v) for v in args.configs.split(",") if v.strip()}
+
     # config 1: N = 2000, FP64 CSR; 100 iterations, exaggeration 12 for 25, lr 1, momentum 0.5
     w = inputs.make_config(1, seed=args.seed, device=dev)
     sched = schedule(100, 25, 12.0, 0.5, 0.5, 1.0)
-    for theta in (0.0, 0.5):
+    for theta in ((0.0, 0.5) if 1 in want else ()):
         line = {"workload": inputs.CONFIG_NAMES[1], "n": w.n, "nnz": w.nnz, "theta": theta,
                 "iterations": 100, "schedule": "25 x (exaggeration 12) + 75 x 1, lr 1, momentum 0.5"}
         line["fp64_gpu"] = gpu_time("fp64", w, w.y0, sched, theta, graphs=True)
@@ -630,6 +633,8 @@ def run_suite(args, rank, world, local):
 
     # configs 2, 3, 5: the paper's protocol, 1000 iterations, lr = N / 12000
     for cfg, thetas in ((2, (0.5,)), (3, (0.2, 0.5, 0.8)), (5, (0.5, 0.8))):
+        if cfg not in want:
+            continue
         w = inputs.make_config(cfg, seed=args.seed, device=dev)
         lr = w.n / 12000.0
         sched = schedule(1000, 250, 12.0, 0.5, 0.8, lr)
@@ -649,6 +654,8 @@ def run_suite(args, rank, world, local):
             emit(line)
 
     # config 4: 64 embeddings in one context, 500 iterations (125 exaggerated), lr = n_s / 12000
+    if 4 not in want:
+        return
     w = inputs.make_batched(64, seed=args.seed, device=dev)
     off = w.extra["offsets"]
     sizes = np.diff(off).astype(np.float64)

@@ -140,6 +140,10 @@ int ensure_points(hts_ctx *c, int64_t n)
     c->scan_tmp_len = scan_tmp_size(std::max<int64_t>(256 * tiles, (int64_t)N + 1));
     AL(c->scan_tmp, (size_t)c->scan_tmp_len);
     AL(c->red_tmp, std::max<size_t>(3 * ((size_t)N * 32 / 256 + 2), 512));  // also >= 6 (N / 1024 + 2)
+    {
+        const int sp = exact_split((int64_t)N);
+        AL(c->exact_part, sp > 1 ? 4 * (size_t)sp * N : 4);
+    }
 #undef AL
     c->n_nodes = c->pre + n;
     c->cap_n = n;
@@ -465,7 +469,7 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->bn_left); dfree(&c->bn_right); dfree(&c->bn_parent); dfree(&c->leaf_parent);
     dfree(&c->bn_lo); dfree(&c->bn_hi); dfree(&c->bn_pref); dfree(&c->bn_flag); dfree(&c->bn_quad);
     dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
-    dfree(&c->sort_scratch); dfree(&c->scan_tmp); dfree(&c->red_tmp); dfree(&c->minmax);
+    dfree(&c->sort_scratch); dfree(&c->scan_tmp); dfree(&c->exact_part); dfree(&c->red_tmp); dfree(&c->minmax);
     dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq);
     dfree(&c->seg_off); dfree(&c->seg_of); dfree(&c->seg_lr); dfree(&c->seg_z);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);

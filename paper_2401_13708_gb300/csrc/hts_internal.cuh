@@ -126,6 +126,7 @@ struct hts_ctx {
 
     // scratch
     unsigned long long *sort_scratch = nullptr;  // digit offsets, tile counters, look-back status words
+    double *exact_part = nullptr;    // exact kernel chunk sums (4 doubles x exact_split(n) x n)
     int *scan_tmp = nullptr;
     int64_t scan_tmp_len = 0;
     double *red_tmp = nullptr;        // reduction partials
@@ -186,6 +187,9 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex);
 // traverse.cu
 void launch_walk(hts_ctx *c);
 void launch_exact(hts_ctx *c);
+// j-chunks of the exact kernel for n points (1 when the i-blocks alone fill
+// the GPU); the partial sums take exact_split(n) * n double4 when it is > 1
+int exact_split(int64_t n);
 // attract.cu
 void launch_attract(hts_ctx *c);
 void launch_kl_terms(hts_ctx *c);
@@ -219,6 +223,20 @@ namespace hts {
 // and the il_i s y_i term are applied once per point at the end.
 // delta is clamped below by a tiny positive number so that coincident
 // points give w = 1 and zero force (the limit of w^2 d dd/dy as d -> 0).
+// Float64 position and 1 / (1 - |y|^2) of a point record.
+__device__ __forceinline__ void point_xy_il(const PointF &q, double &x, double &y, double &il)
+{
+    x = (double)q.xh + (double)q.xl;
+    y = (double)q.yh + (double)q.yl;
+    il = (double)q.il;
+}
+__device__ __forceinline__ void point_xy_il(const PointD &q, double &x, double &y, double &il)
+{
+    x = q.x;
+    y = q.y;
+    il = q.il;
+}
+
 struct PairF {
     float w, rep, att;  // w, w^2 d / t (or w^2 / t), w d / t (or w / t)
 };

@@ -32,7 +32,7 @@ namespace hts {
 namespace {
 
 constexpr int kWalkBlock = 256;
-constexpr int kExactBlock = 256;
+constexpr int kExactBlock = 64;
 
 __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int k)
 {
@@ -295,33 +295,57 @@ __global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD
 }
 
 
-// Exact repulsion: one thread per point i, tiles of 256 points j staged in
-// shared memory, every pair j != i.
+// Exact repulsion: one thread per point i, tiles of kExactBlock points j
+// staged in shared memory, every pair j != i of the same segment.  A small
+// problem has too few i-blocks to fill the GPU, so the j range of each
+// i-block is cut into `split` chunks (grid.y): with split == 1 the block
+// writes the finished force and Z_i, otherwise raw sums per chunk go to
+// `part` and exact_combine_kernel adds them in chunk order (deterministic).
+struct ExactArgs {
+    int n, split;
+    double2 *frep;
+    double *zi;
+    double4_32a *part;  // [split][n]: sums of k Delta_x, k Delta_y, k s, w
+    const unsigned char *seg_of;
+    const int64_t *seg_off;
+};
+
+__device__ __forceinline__ void exact_ranges(const ExactArgs &A, int i, int &jlo, int &jhi, int &cbeg, int &cend)
+{
+    // own segment [jlo, jhi); the union over the block's threads, cut into chunks
+    int blo = 0, bhi = A.n;
+    jlo = 0;
+    jhi = A.n;
+    if (A.seg_of) {
+        const int first = blockIdx.x * kExactBlock, last = min(first + kExactBlock, A.n) - 1;
+        const int si = A.seg_of[i < A.n ? i : A.n - 1];
+        jlo = (int)A.seg_off[si];
+        jhi = (int)A.seg_off[si + 1];
+        blo = (int)A.seg_off[A.seg_of[first]];
+        bhi = (int)A.seg_off[A.seg_of[last] + 1];
+    }
+    const int tiles = (bhi - blo + kExactBlock - 1) / kExactBlock;
+    const int per = (tiles + A.split - 1) / A.split;
+    cbeg = min(bhi, blo + (int)blockIdx.y * per * kExactBlock);
+    cend = min(bhi, cbeg + per * kExactBlock);
+}
+
 template <int GF>
-__global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(int n, const PointF *__restrict__ pts, double2 *frep,
-                                                                double *zi, const unsigned char *__restrict__ seg_of,
-                                                                const int64_t *__restrict__ seg_off)
+__global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(const PointF *__restrict__ pts, ExactArgs A)
 {
     __shared__ PointF tile[kExactBlock];
+    const int n = A.n;
     const int i = blockIdx.x * kExactBlock + threadIdx.x;
-    // own segment [jlo, jhi) and the union over the block's threads [blo, bhi)
-    int jlo = 0, jhi = n, blo = 0, bhi = n;
-    if (seg_of) {
-        const int first = blockIdx.x * kExactBlock, last = min(first + kExactBlock, n) - 1;
-        const int si = seg_of[i < n ? i : n - 1];
-        jlo = (int)seg_off[si];
-        jhi = (int)seg_off[si + 1];
-        blo = (int)seg_off[seg_of[first]];
-        bhi = (int)seg_off[seg_of[last] + 1];
-    }
+    int jlo, jhi, cbeg, cend;
+    exact_ranges(A, i, jlo, jhi, cbeg, cend);
     const PointF q = pts[i < n ? i : n - 1];
     const float twoil = 2.0f * q.il;
     float rx = 0.f, ry = 0.f, rs = 0.f, z = 0.f;
-    for (int base = blo; base < bhi; base += kExactBlock) {
+    for (int base = cbeg; base < cend; base += kExactBlock) {
         int j = base + threadIdx.x;
-        if (j < bhi) tile[threadIdx.x] = pts[j];
+        if (j < cend) tile[threadIdx.x] = pts[j];
         __syncthreads();
-        const int cnt = min(kExactBlock, bhi - base);
+        const int cnt = min(kExactBlock, cend - base);
         for (int k = 0; k < cnt; ++k) {
             const int jj = base + k;
             if (jj == i || jj < jlo || jj >= jhi) continue;
@@ -338,40 +362,34 @@ __global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(int n, const Poi
         }
         __syncthreads();
     }
-    if (i < n) {
-        double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
-        double il = (double)q.il;
-        double rsd = il * (double)rs;
-        frep[i] = make_double2(4.0 * il * ((double)rx + rsd * x), 4.0 * il * ((double)ry + rsd * y));
-        zi[i] = (double)z;
+    if (i >= n) return;
+    if (A.split > 1) {
+        A.part[(size_t)blockIdx.y * n + i] = make_double4_32a(rx, ry, rs, z);
+        return;
     }
+    double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
+    double il = (double)q.il;
+    double rsd = il * (double)rs;
+    A.frep[i] = make_double2(4.0 * il * ((double)rx + rsd * x), 4.0 * il * ((double)ry + rsd * y));
+    A.zi[i] = (double)z;
 }
 
 template <int GF>
-__global__ void __launch_bounds__(kExactBlock) exact_f64_kernel(int n, const PointD *__restrict__ pts, double2 *frep,
-                                                                double *zi, const unsigned char *__restrict__ seg_of,
-                                                                const int64_t *__restrict__ seg_off)
+__global__ void __launch_bounds__(kExactBlock) exact_f64_kernel(const PointD *__restrict__ pts, ExactArgs A)
 {
     __shared__ PointD tile[kExactBlock];
+    const int n = A.n;
     const int i = blockIdx.x * kExactBlock + threadIdx.x;
-    // own segment [jlo, jhi) and the union over the block's threads [blo, bhi)
-    int jlo = 0, jhi = n, blo = 0, bhi = n;
-    if (seg_of) {
-        const int first = blockIdx.x * kExactBlock, last = min(first + kExactBlock, n) - 1;
-        const int si = seg_of[i < n ? i : n - 1];
-        jlo = (int)seg_off[si];
-        jhi = (int)seg_off[si + 1];
-        blo = (int)seg_off[seg_of[first]];
-        bhi = (int)seg_off[seg_of[last] + 1];
-    }
+    int jlo, jhi, cbeg, cend;
+    exact_ranges(A, i, jlo, jhi, cbeg, cend);
     const PointD q = pts[i < n ? i : n - 1];
     const double twoil = 2.0 * q.il;
     double rx = 0, ry = 0, rs = 0, z = 0;
-    for (int base = blo; base < bhi; base += kExactBlock) {
+    for (int base = cbeg; base < cend; base += kExactBlock) {
         int j = base + threadIdx.x;
-        if (j < bhi) tile[threadIdx.x] = pts[j];
+        if (j < cend) tile[threadIdx.x] = pts[j];
         __syncthreads();
-        const int cnt = min(kExactBlock, bhi - base);
+        const int cnt = min(kExactBlock, cend - base);
         for (int k = 0; k < cnt; ++k) {
             const int jj = base + k;
             if (jj == i || jj < jlo || jj >= jhi) continue;
@@ -387,11 +405,36 @@ __global__ void __launch_bounds__(kExactBlock) exact_f64_kernel(int n, const Poi
         }
         __syncthreads();
     }
-    if (i < n) {
-        double rsd = q.il * rs;
-        frep[i] = make_double2(4.0 * q.il * (rx + rsd * q.x), 4.0 * q.il * (ry + rsd * q.y));
-        zi[i] = z;
+    if (i >= n) return;
+    if (A.split > 1) {
+        A.part[(size_t)blockIdx.y * n + i] = make_double4_32a(rx, ry, rs, z);
+        return;
     }
+    double rsd = q.il * rs;
+    A.frep[i] = make_double2(4.0 * q.il * (rx + rsd * q.x), 4.0 * q.il * (ry + rsd * q.y));
+    A.zi[i] = z;
+}
+
+// Sums of the chunks of each point in chunk order, then the per-point factors.
+template <typename PT>
+__global__ void exact_combine_kernel(const PT *__restrict__ pts, ExactArgs A)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    double rx = 0, ry = 0, rs = 0, z = 0;
+    for (int c = 0; c < A.split; ++c) {
+        const double4_32a v = A.part[(size_t)c * A.n + i];
+        rx += v.x;
+        ry += v.y;
+        rs += v.z;
+        z += v.w;
+    }
+    const PT q = pts[i];
+    double x, y, il;
+    point_xy_il(q, x, y, il);
+    const double rsd = il * rs;
+    A.frep[i] = make_double2(4.0 * il * (rx + rsd * x), 4.0 * il * (ry + rsd * y));
+    A.zi[i] = z;
 }
 
 }  // namespace
@@ -426,23 +469,39 @@ void launch_walk(hts_ctx *c)
 #undef HTS_WALK
 }
 
+int exact_split(int64_t n)
+{
+    constexpr int64_t kTargetBlocks = 1216;  // 8 blocks of 64 threads on each of 152 SMs
+    const int64_t blocks = (n + kExactBlock - 1) / kExactBlock;
+    if (blocks <= 0 || blocks >= kTargetBlocks) return 1;
+    return (int)std::min<int64_t>(blocks, (kTargetBlocks + blocks - 1) / blocks);
+}
+
 void launch_exact(hts_ctx *c)
 {
-    const int n = (int)c->n;
-    const int blocks = (n + kExactBlock - 1) / kExactBlock;
-    const unsigned char *so = c->nseg > 1 ? c->seg_of : nullptr;
-    const int64_t *sf = c->seg_off;
-    c->launches += 1;
+    ExactArgs A;
+    A.n = (int)c->n;
+    A.split = exact_split(c->n);
+    A.frep = c->frep;
+    A.zi = c->zi;
+    A.part = reinterpret_cast<double4_32a *>(c->exact_part);
+    A.seg_of = c->nseg > 1 ? c->seg_of : nullptr;
+    A.seg_off = c->seg_off;
+    const dim3 grid((unsigned)((A.n + kExactBlock - 1) / kExactBlock), (unsigned)A.split);
+    const int cb = (A.n + 255) / 256;
+    c->launches += A.split > 1 ? 2 : 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
         if (c->cfg.grad_form == HTS_EXACT_KL)
-            exact_f32_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi, so, sf);
+            exact_f32_kernel<0><<<grid, kExactBlock, 0, c->stream>>>(c->pts32, A);
         else
-            exact_f32_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts32, c->frep, c->zi, so, sf);
+            exact_f32_kernel<1><<<grid, kExactBlock, 0, c->stream>>>(c->pts32, A);
+        if (A.split > 1) exact_combine_kernel<PointF><<<cb, 256, 0, c->stream>>>(c->pts32, A);
     } else {
         if (c->cfg.grad_form == HTS_EXACT_KL)
-            exact_f64_kernel<0><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi, so, sf);
+            exact_f64_kernel<0><<<grid, kExactBlock, 0, c->stream>>>(c->pts64, A);
         else
-            exact_f64_kernel<1><<<blocks, kExactBlock, 0, c->stream>>>(n, c->pts64, c->frep, c->zi, so, sf);
+            exact_f64_kernel<1><<<grid, kExactBlock, 0, c->stream>>>(c->pts64, A);
+        if (A.split > 1) exact_combine_kernel<PointD><<<cb, 256, 0, c->stream>>>(c->pts64, A);
     }
 }
 
