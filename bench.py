@@ -628,6 +628,7 @@ def run_suite(args, rank, world, local):
                 "iterations": 100, "schedule": "25 x (exaggeration 12) + 75 x 1, lr 1, momentum 0.5"}
         line["fp64_gpu"] = gpu_time("fp64", w, w.y0, sched, theta, graphs=True)
         line["fp32_mixed_gpu"] = gpu_time("fp32", w, w.y0, sched, theta, graphs=True)
+        line["fp32_mixed_gpu_eager"] = gpu_time("fp32", w, w.y0, sched, theta)
         line["oracle"] = oracle_iters(w, w.y0, 100, theta, 12.0, 1.0, 0.5)
         emit(line)
 
