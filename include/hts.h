@@ -272,6 +272,18 @@ HTS_API int hts_set_graphs(hts_ctx *ctx, int enable);
  * HTS_EINVAL (theta outside [0, 1], reps outside [1, 1000], a value not in
  * the lists), HTS_ECUDA. */
 HTS_API int hts_autotune(hts_ctx *ctx, double theta, int reps, int *tuning);
+
+/* Split walk for small problems (one embedding; no counterpart in the
+ * paper).  With few 32-point chunks the walk cannot fill the GPU, so each
+ * chunk is walked by up to 4^depth warps, one per subtree of the tree cut at
+ * `depth` (0..3) below the root, which is never accepted; a warp first
+ * evaluates the criterion at its subtree's ancestors, and the interaction
+ * with an accepted ancestor is counted by one warp only, so every point gets
+ * exactly the interactions of its own walk (the partial sums are added in a
+ * fixed order).  depth = -1 (default) picks the shallowest cut that gives
+ * about 2048 warps (8192 in HTS_FP64), within a partial-sum buffer of
+ * min(64 n, 2^22) entries for n <= 262144 (no split above).  Errors: HTS_EINVAL (depth < -1 or > 3). */
+HTS_API int hts_set_walk_split(hts_ctx *ctx, int depth);
 HTS_API int hts_set_tuning(hts_ctx *ctx, int walk_block, int attract_lanes);
 HTS_API int hts_get_tuning(const hts_ctx *ctx, int *tuning);
 

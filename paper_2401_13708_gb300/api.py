@@ -196,6 +196,10 @@ class HyperbolicTSNE:
     def set_tuning(self, walk_block: int = 0, attract_lanes: int = 0):
         self._check(self._lib.hts_set_tuning(self._ctx, int(walk_block), int(attract_lanes)))
 
+    def set_walk_split(self, depth: int = -1):
+        """Cut depth (0..3) of the split walk for small problems; -1 chooses by size."""
+        self._check(self._lib.hts_set_walk_split(self._ctx, int(depth)))
+
     def get_tuning(self):
         out = (C.c_int * 2)()
         self._check(self._lib.hts_get_tuning(self._ctx, out))

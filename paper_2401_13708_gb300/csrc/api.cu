@@ -143,6 +143,19 @@ int ensure_points(hts_ctx *c, int64_t n)
     {
         const int sp = exact_split((int64_t)N);
         AL(c->exact_part, sp > 1 ? 4 * (size_t)sp * N : 4);
+        const int cap = walk_split_capacity((int64_t)N);  // split walk partial sums (float4 / double4)
+        double *part = (double *)c->split_part, *fr = (double *)c->split_frontier;
+        c->split_part = nullptr;
+        c->split_frontier = nullptr;
+        if (part) cudaFree(part);
+        if (fr) cudaFree(fr);
+        if ((r = dalloc(c, &part, cap > 0 ? 4 * (size_t)cap * N : 4))) return r;
+        if ((r = dalloc(c, &fr, walk_split_frontier_bytes() / sizeof(double) + 1))) {
+            cudaFree(part);
+            return r;
+        }
+        c->split_part = part;
+        c->split_frontier = fr;
     }
 #undef AL
     c->n_nodes = c->pre + n;
@@ -492,7 +505,9 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->bn_left); dfree(&c->bn_right); dfree(&c->bn_parent); dfree(&c->leaf_parent);
     dfree(&c->bn_lo); dfree(&c->bn_hi); dfree(&c->bn_pref); dfree(&c->bn_flag); dfree(&c->bn_quad);
     dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
-    dfree(&c->sort_scratch); dfree(&c->scan_tmp); dfree(&c->exact_part); dfree(&c->red_tmp); dfree(&c->minmax);
+    dfree(&c->sort_scratch); dfree(&c->scan_tmp); dfree(&c->exact_part);
+    if (c->split_part) cudaFree(c->split_part);
+    if (c->split_frontier) cudaFree(c->split_frontier); dfree(&c->red_tmp); dfree(&c->minmax);
     dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq);
     dfree(&c->seg_off); dfree(&c->seg_of); dfree(&c->seg_lr); dfree(&c->seg_z);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -1159,6 +1174,16 @@ int hts_set_tuning(hts_ctx *c, int walk_block, int attract_lanes)
         return fail(c, HTS_EINVAL, "hts_set_tuning: walk_block in {32,64,128,256}, attract_lanes in {4,8,16,32}");
     if (walk_block) c->walk_block = walk_block;
     if (attract_lanes) c->attract_group = attract_lanes;
+    c->layout_version += 1;
+    return HTS_OK;
+}
+
+int hts_set_walk_split(hts_ctx *c, int depth)
+{
+    if (!c) return HTS_EINVAL;
+    c->err.clear();
+    if (depth < -1 || depth > 3) return fail(c, HTS_EINVAL, "hts_set_walk_split: depth in -1 .. 3");
+    c->walk_split = depth;
     c->layout_version += 1;
     return HTS_OK;
 }

@@ -157,6 +157,9 @@ struct hts_ctx {
     // launch shapes (hts_autotune / hts_set_tuning)
     int walk_block = 256;            // walk threads per block: 32, 64, 128 or 256
     int attract_group = 8;           // float32 attraction lanes per row of P: 4, 8, 16 or 32
+    int walk_split = -1;             // cut depth of the split walk (-1: by problem size)
+    void *split_frontier = nullptr;  // frontier table + entry count
+    void *split_part = nullptr;      // partial sums of the split walk
 
     // CO-SNE term (Sec. 4.3): lambda1 KL + lambda2 (1/n) sum (|x|^2 - |y|^2)^2
     double cosne_l1 = 1.0, cosne_l2 = 0.0;
@@ -190,6 +193,11 @@ void launch_exact(hts_ctx *c);
 // j-chunks of the exact kernel for n points (1 when the i-blocks alone fill
 // the GPU); the partial sums take exact_split(n) * n double4 when it is > 1
 int exact_split(int64_t n);
+// split walk: buffer capacity (frontier entries) for n points, the depth used,
+// and the bytes of the frontier table
+int walk_split_capacity(int64_t n);
+int walk_split_depth(int64_t n, int want, bool fp64);
+size_t walk_split_frontier_bytes();
 // attract.cu
 void launch_attract(hts_ctx *c);
 void launch_kl_terms(hts_ctx *c);

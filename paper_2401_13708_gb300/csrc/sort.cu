@@ -266,6 +266,90 @@ int scan_exclusive(const int *in, int *out, int64_t len, int *tmp, cudaStream_t 
     return k + 2;
 }
 
+namespace {
+
+// n <= kTile: all eight passes in one block (no look-back: the block's own
+// histogram is the global one), ping-ponging through the two key buffers.
+__global__ void __launch_bounds__(kSortThreads) small_sort_kernel(uint64_t *ka, uint32_t *va, uint64_t *kb,
+                                                                  uint32_t *vb, int n)
+{
+    __shared__ int wh[kWarps][256];
+    __shared__ int dsum[256];
+    __shared__ int wtot[kWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int base = w * kPerWarp;
+    for (int p = 0; p < kPasses; ++p) {
+        const uint64_t *kin = (p & 1) ? kb : ka;
+        const uint32_t *vin = (p & 1) ? vb : va;
+        uint64_t *kout = (p & 1) ? ka : kb;
+        uint32_t *vout = (p & 1) ? va : vb;
+        const int shift = 8 * p;
+        for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
+        __syncthreads();
+        uint64_t key[kRounds];
+        uint32_t val[kRounds];
+        int dig[kRounds];
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int i = base + r * 32 + lane;
+            const bool ok = i < n;
+            key[r] = ok ? kin[i] : 0ull;
+            val[r] = ok ? vin[i] : 0u;
+            dig[r] = ok ? (int)((key[r] >> shift) & 0xFFu) : 256 + lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+            if (ok && (peers & lt) == 0u) wh[w][dig[r]] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) {
+                const int t = wh[k][d];
+                wh[k][d] = cnt;
+                cnt += t;
+            }
+            // exclusive scan of the 256 digit counts: warp scans, then warp totals
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) wtot[w] = incl;
+            dsum[d] = incl - cnt;
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            int off = dsum[d];
+            for (int k = 0; k < w; ++k) off += wtot[k];
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) wh[k][d] += off;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int i = base + r * 32 + lane;
+            const bool ok = i < n;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+            int pos = 0;
+            if (ok) pos = wh[w][dig[r]] + __popc(peers & lt);
+            __syncwarp();
+            if (ok && (peers & lt) == 0u) wh[w][dig[r]] += __popc(peers);
+            __syncwarp();
+            if (ok && pos >= 0 && pos < n) {
+                kout[pos] = key[r];
+                vout[pos] = val[r];
+            }
+        }
+        __syncthreads();  // this pass's output is the next pass's input
+    }
+}
+
+}  // namespace
+
 size_t sort_status_words(int64_t n)
 {
     const int64_t tiles = (n + kTile - 1) / kTile;
@@ -276,6 +360,11 @@ void launch_sort_pairs(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int tiles = (n + kTile - 1) / kTile;
+    if (tiles == 1) {  // one block does all eight passes
+        small_sort_kernel<<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt, n);
+        c->launches += 1;
+        return;
+    }
     // scratch: 2048 ints of digit offsets, 8 tile counters, then the status words
     int *hist = reinterpret_cast<int *>(c->sort_scratch);
     int *ctr = hist + kPasses * 256;

@@ -68,13 +68,43 @@ __device__ __forceinline__ void segment_range(const SegView &sv, int p, int m, i
     end = min(sv.pre[sv.off[sg + 1]], m);
 }
 
-// One warp walks for the 32 sorted points of chunk `warp`.
-template <int GF, bool COUNT, bool SEG>
+// Split walk (small problems, one embedding): the root is never accepted
+// (every point lies inside it, and r_cell / d >= 1 > theta), so each point's
+// walk is the union of its walks of the subtrees below a cut of the tree at
+// depth D.  One warp takes one 32-point chunk and one subtree of the cut (a
+// "frontier" entry): it first evaluates the criterion at the entry's
+// ancestors (depth 1 .. D-1) -- a lane that accepts one is done with this
+// subtree, and the interaction with that ancestor is counted by the first
+// frontier entry below it only -- then walks the subtree.  The partial sums
+// of the entries are added in entry order by walk_combine_kernel, so every
+// lane gets exactly the interactions of its full walk.
+constexpr int kMaxSplitDepth = 3;
+constexpr int kMaxFrontier = 64;           // 4^3
+constexpr int64_t kSplitMaxN = 262144;     // larger problems fill the GPU with chunks alone
+constexpr int64_t kSplitEntries = 1 << 22; // partial-sum buffer: entries x points
+
+struct Frontier {
+    int node;                         // subtree root
+    int nanc;                         // ancestors below the root
+    int anc[kMaxSplitDepth];
+    int own;                          // bit k: this entry counts an accepted anc[k]
+};
+
+struct SplitView {
+    const Frontier *fr;               // nullptr: no split
+    const int *count;                 // frontier entries
+    void *part;                       // [entry][n] partial sums (float4 / double4)
+};
+
+// One warp walks for the 32 sorted points of chunk `warp` (and, split, the
+// frontier entry `fi`).
+template <int GF, bool COUNT, bool SEG, bool SPLIT>
 __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__restrict__ nodes,
                                                 const int *__restrict__ n_nodes,
                                                 const PointF *__restrict__ spts,
                                                 const uint32_t *__restrict__ idx, double2 *frep, double *zi,
-                                                unsigned long long *counters, const SegView sv)
+                                                unsigned long long *counters, const SegView sv,
+                                                const SplitView sp, int fi)
 {
     const int lane = threadIdx.x & 31;
     const int p = warp * 32 + lane;
@@ -85,10 +115,38 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
     const int m = min(*n_nodes, 2 * n);
     int root = 0, end = m;
     if (SEG) segment_range(sv, valid ? p : n - 1, m, root, end);
-    int resume = valid ? root : INT_MAX;
-    int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : 0;  // lane 0 holds the first segment
-    const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : m;
     unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
+    bool live = valid;
+    if (SPLIT) {  // frontier entry: ancestors first, then the subtree [node, skip)
+        const Frontier F = sp.fr[fi];
+#pragma unroll
+        for (int k = 0; k < kMaxSplitDepth; ++k) {
+            if (k >= F.nanc) break;
+            const NodeF a = load_node(nodes, F.anc[k]);
+            float dx = (q.xh - a.xh) + (q.xl - a.xl);
+            float dy = (q.yh - a.yh) + (q.yl - a.yl);
+            float s = fmaf(dx, dx, dy * dy);
+            float delta = s * twoil * a.il;
+            if (live && delta > a.thr) {
+                if ((F.own >> k) & 1) {
+                    PairF t = pair_terms_f32<GF>(delta);
+                    float mult = (float)a.count;
+                    float kk = mult * t.rep * a.il;
+                    rx = fmaf(kk, dx, rx);
+                    ry = fmaf(kk, dy, ry);
+                    rs = fmaf(kk, s, rs);
+                    z = fmaf(mult, t.w, z);
+                    if (COUNT) ++c_acc;
+                }
+                live = false;
+            }
+        }
+        root = F.node;
+        end = min(load_node(nodes, F.node).skip, m);
+    }
+    int resume = live ? root : INT_MAX;
+    int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : root;  // lane 0 holds the first segment
+    const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : end;
     while (node < stop) {
         const NodeF c = load_node(nodes, node);
         const bool active = node >= resume && (!SEG || node < end);
@@ -148,7 +206,9 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
         // no cell otherwise) and unwritten slots are zero (empty buckets)
         node = next;
     }
-    if (valid) {
+    if (SPLIT && valid) {
+        reinterpret_cast<float4 *>(sp.part)[(size_t)fi * n + p] = make_float4(rx, ry, rs, z);
+    } else if (valid) {
         const uint32_t i = idx[p];
         double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
         double il = (double)q.il;
@@ -173,25 +233,27 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
 // One warp per chunk of 32 sorted points; the warps of a block (blockDim.x /
 // 32 <= kWalkBlock / 32, picked by the autotuner) take consecutive chunks, so
 // their walks share node data in L1.  The block size does not change results.
-template <int GF, bool COUNT, bool SEG>
+template <int GF, bool COUNT, bool SEG, bool SPLIT>
 __global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF *__restrict__ nodes,
                                                               const int *__restrict__ n_nodes,
                                                               const PointF *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              const SegView sv)
+                                                              const SegView sv, const SplitView sp)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp * 32 >= n) return;
-    walk_f32_chunk<GF, COUNT, SEG>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv);
+    if (SPLIT && (int)blockIdx.y >= *sp.count) return;
+    walk_f32_chunk<GF, COUNT, SEG, SPLIT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv, sp, blockIdx.y);
 }
 
-template <int GF, bool COUNT, bool SEG>
+template <int GF, bool COUNT, bool SEG, bool SPLIT>
 __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__restrict__ nodes,
                                                 const int *__restrict__ n_nodes,
                                                 const PointD *__restrict__ spts,
                                                 const uint32_t *__restrict__ idx, double2 *frep, double *zi,
-                                                unsigned long long *counters, const SegView sv)
+                                                unsigned long long *counters, const SegView sv,
+                                                const SplitView sp, int fi)
 {
     const int lane = threadIdx.x & 31;
     const int p = warp * 32 + lane;
@@ -202,10 +264,37 @@ __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__r
     const int m = min(*n_nodes, 2 * n);
     int root = 0, end = m;
     if (SEG) segment_range(sv, valid ? p : n - 1, m, root, end);
-    int resume = valid ? root : INT_MAX;
-    int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : 0;
-    const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : m;
     unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
+    bool live = valid;
+    if (SPLIT) {  // as in the float32 walk
+        const Frontier F = sp.fr[fi];
+#pragma unroll
+        for (int k = 0; k < kMaxSplitDepth; ++k) {
+            if (k >= F.nanc) break;
+            const NodeD a = nodes[F.anc[k]];
+            double dx = q.x - a.x, dy = q.y - a.y;
+            double s = fma(dx, dx, dy * dy);
+            double delta = s * twoil * a.il;
+            if (live && delta > a.thr) {
+                if ((F.own >> k) & 1) {
+                    PairD t = pair_terms_f64<GF>(delta);
+                    double mult = (double)a.count;
+                    double kk = mult * t.rep * a.il;
+                    rx = fma(kk, dx, rx);
+                    ry = fma(kk, dy, ry);
+                    rs = fma(kk, s, rs);
+                    z = fma(mult, t.w, z);
+                    if (COUNT) ++c_acc;
+                }
+                live = false;
+            }
+        }
+        root = F.node;
+        end = min(nodes[F.node].skip, m);
+    }
+    int resume = live ? root : INT_MAX;
+    int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : root;
+    const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : end;
     while (node < stop) {
         const NodeD c = nodes[node];
         const bool active = node >= resume && (!SEG || node < end);
@@ -260,7 +349,9 @@ __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__r
         if (COUNT && lane == 0) ++c_visit;
         node = next;  // as in the float32 walk
     }
-    if (valid) {
+    if (SPLIT && valid) {
+        reinterpret_cast<double4_32a *>(sp.part)[(size_t)fi * n + p] = make_double4_32a(rx, ry, rs, z);
+    } else if (valid) {
         const uint32_t i = idx[p];
         double rsd = q.il * rs;
         frep[i] = make_double2(4.0 * q.il * (rx + rsd * q.x), 4.0 * q.il * (ry + rsd * q.y));
@@ -281,17 +372,101 @@ __device__ __forceinline__ void walk_f64_chunk(int warp, int n, const NodeD *__r
 }
 
 // As walk_f32_kernel, in float64.
-template <int GF, bool COUNT, bool SEG>
+template <int GF, bool COUNT, bool SEG, bool SPLIT>
 __global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD *__restrict__ nodes,
                                                               const int *__restrict__ n_nodes,
                                                               const PointD *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              const SegView sv)
+                                                              const SegView sv, const SplitView sp)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp * 32 >= n) return;
-    walk_f64_chunk<GF, COUNT, SEG>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv);
+    if (SPLIT && (int)blockIdx.y >= *sp.count) return;
+    walk_f64_chunk<GF, COUNT, SEG, SPLIT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv, sp, blockIdx.y);
+}
+
+// The frontier of the cut at `depth` (single thread; at most 4^depth entries
+// in pre-order).  A cell with more than 4 children or a skip that does not
+// advance is a broken tree: status bit 2, no entries (the walk then does no
+// work and the error is reported).
+template <typename NT>
+__global__ void frontier_kernel(const NT *__restrict__ nodes, const int *__restrict__ n_nodes, int n, int depth,
+                                Frontier *fr, int *count, int *status)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int m = min(*n_nodes, 2 * n);
+    Frontier a[kMaxFrontier], b[kMaxFrontier];
+    int na = 1;
+    a[0].node = 0;
+    a[0].nanc = 0;
+    a[0].own = 0;
+    bool bad = m <= 0;
+    for (int d = 0; d < depth && !bad; ++d) {
+        int nb = 0;
+        for (int e = 0; e < na && !bad; ++e) {
+            const Frontier &E = a[e];
+            const NT c = nodes[E.node];
+            const int cnt = c.count & 0x7fffffff;
+            if (c.count < 2 || cnt < 2) {  // leaf or bucket: stays an entry
+                if (nb >= kMaxFrontier) { bad = true; break; }
+                b[nb++] = E;
+                continue;
+            }
+            bool first = true;
+            int kids = 0;
+            for (int ch = E.node + 1; ch < c.skip && ch < m;) {
+                if (++kids > 4 || nb >= kMaxFrontier) { bad = true; break; }
+                Frontier F = E;
+                F.node = ch;
+                F.own = first ? E.own : 0;
+                if (d >= 1) {  // E is below the root: an ancestor of its children
+                    F.anc[F.nanc] = E.node;
+                    if (first) F.own |= 1 << F.nanc;
+                    F.nanc += 1;
+                }
+                b[nb++] = F;
+                first = false;
+                const int nx = nodes[ch].skip;
+                if (nx <= ch) { bad = true; break; }
+                ch = nx;
+            }
+        }
+        for (int e = 0; e < nb; ++e) a[e] = b[e];
+        na = nb;
+    }
+    if (bad) {
+        atomicOr(status, 2);
+        na = 0;
+    }
+    for (int e = 0; e < na; ++e) fr[e] = a[e];
+    *count = na;
+}
+
+// Sorted point p: the frontier entries' partial sums in entry order, then the
+// per-point factors.
+template <typename PT, typename VT>
+__global__ void walk_combine_kernel(int n, const PT *__restrict__ spts, const uint32_t *__restrict__ idx,
+                                    const VT *__restrict__ part, const int *__restrict__ count, double2 *frep,
+                                    double *zi)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int nf = *count;
+    double rx = 0, ry = 0, rs = 0, z = 0;
+    for (int e = 0; e < nf; ++e) {
+        const VT v = part[(size_t)e * n + p];
+        rx += (double)v.x;
+        ry += (double)v.y;
+        rs += (double)v.z;
+        z += (double)v.w;
+    }
+    double x, y, il;
+    point_xy_il(spts[p], x, y, il);
+    const double rsd = il * rs;
+    const uint32_t i = idx[p];
+    frep[i] = make_double2(4.0 * il * (rx + rsd * x), 4.0 * il * (ry + rsd * y));
+    zi[i] = z;
 }
 
 
@@ -439,26 +614,67 @@ __global__ void exact_combine_kernel(const PT *__restrict__ pts, ExactArgs A)
 
 }  // namespace
 
+int walk_split_capacity(int64_t n)
+{
+    // frontier entries x points of the partial-sum buffer (0: no split)
+    if (n <= 0 || n > kSplitMaxN) return 0;
+    return (int)std::min<int64_t>(kMaxFrontier, kSplitEntries / n);
+}
+
+// Cut depth for n points: the shallowest that gives about 2048 warps (8192
+// for the float64 walk, whose long float64 latencies need more warps to
+// hide), within the buffer; `want` >= 0 overrides (clamped), -1 chooses.
+int walk_split_depth(int64_t n, int want, bool fp64)
+{
+    const int cap = walk_split_capacity(n);
+    int dmax = 0;
+    while (dmax < kMaxSplitDepth && (1 << (2 * (dmax + 1))) <= cap) ++dmax;
+    if (want >= 0) return std::min(want, dmax);
+    const int64_t chunks = (n + 31) / 32, target = fp64 ? 8192 : 2048;
+    int d = 0;
+    while (d < dmax && chunks * (1 << (2 * d)) < target) ++d;
+    return d;
+}
+
 void launch_walk(hts_ctx *c)
 {
     const int n = (int)c->n;
     const int warps = (n + 31) / 32;
     const int wb = c->walk_block;  // 32 .. kWalkBlock threads, a multiple of 32
-    const int blocks = (warps * 32 + wb - 1) / wb;
     const bool cnt = c->counters_on != 0;  // counters accumulate while enabled
     const bool seg = c->nseg > 1;
     const SegView sv{c->keys, c->seg_off, c->pre};
+    const int depth = seg ? 0 : walk_split_depth(n, c->walk_split, c->cfg.precision == HTS_FP64);
+    SplitView sp{nullptr, nullptr, nullptr};
+    dim3 grid((unsigned)((warps * 32 + wb - 1) / wb), 1);
+    if (depth > 0) {
+        Frontier *fr = reinterpret_cast<Frontier *>(c->split_frontier);
+        int *fcount = reinterpret_cast<int *>(fr + kMaxFrontier);
+        if (c->cfg.precision == HTS_FP32_MIXED)
+            frontier_kernel<NodeF><<<1, 32, 0, c->stream>>>(c->nodes32, c->n_nodes, n, depth, fr, fcount, c->status);
+        else
+            frontier_kernel<NodeD><<<1, 32, 0, c->stream>>>(c->nodes64, c->n_nodes, n, depth, fr, fcount, c->status);
+        c->launches += 1;
+        sp = SplitView{fr, fcount, c->split_part};
+        grid.y = 1u << (2 * depth);
+    }
     c->launches += 1;
-#define HTS_WALK(P, NODES, SPTS, GF, CT, SG)                                                             \
-    walk_##P##_kernel<GF, CT, SG><<<blocks, wb, 0, c->stream>>>(n, NODES, c->n_nodes, SPTS, c->idx, \
-                                                                         c->frep, c->zi, c->counters, sv)
-#define HTS_WALK_ALL(P, NODES, SPTS)                                                   \
-    if (c->cfg.grad_form == HTS_EXACT_KL) {                                             \
-        if (cnt) { if (seg) HTS_WALK(P, NODES, SPTS, 0, true, true); else HTS_WALK(P, NODES, SPTS, 0, true, false); } \
-        else { if (seg) HTS_WALK(P, NODES, SPTS, 0, false, true); else HTS_WALK(P, NODES, SPTS, 0, false, false); } \
-    } else {                                                                            \
-        if (cnt) { if (seg) HTS_WALK(P, NODES, SPTS, 1, true, true); else HTS_WALK(P, NODES, SPTS, 1, true, false); } \
-        else { if (seg) HTS_WALK(P, NODES, SPTS, 1, false, true); else HTS_WALK(P, NODES, SPTS, 1, false, false); } \
+#define HTS_WALK(P, NODES, SPTS, GF, CT, SG, SPL)                                                    \
+    walk_##P##_kernel<GF, CT, SG, SPL><<<grid, wb, 0, c->stream>>>(n, NODES, c->n_nodes, SPTS, c->idx,   \
+                                                                   c->frep, c->zi, c->counters, sv, sp)
+#define HTS_WALK_GF(P, NODES, SPTS, GF)                                                                   \
+    if (depth > 0) {                                                                                       \
+        if (cnt) HTS_WALK(P, NODES, SPTS, GF, true, false, true); else HTS_WALK(P, NODES, SPTS, GF, false, false, true); \
+    } else if (cnt) {                                                                                      \
+        if (seg) HTS_WALK(P, NODES, SPTS, GF, true, true, false); else HTS_WALK(P, NODES, SPTS, GF, true, false, false); \
+    } else {                                                                                               \
+        if (seg) HTS_WALK(P, NODES, SPTS, GF, false, true, false); else HTS_WALK(P, NODES, SPTS, GF, false, false, false); \
+    }
+#define HTS_WALK_ALL(P, NODES, SPTS)                                \
+    if (c->cfg.grad_form == HTS_EXACT_KL) {                          \
+        HTS_WALK_GF(P, NODES, SPTS, 0)                               \
+    } else {                                                         \
+        HTS_WALK_GF(P, NODES, SPTS, 1)                               \
     }
     if (c->cfg.precision == HTS_FP32_MIXED) {
         HTS_WALK_ALL(f32, c->nodes32, c->spts32)
@@ -466,8 +682,24 @@ void launch_walk(hts_ctx *c)
         HTS_WALK_ALL(f64, c->nodes64, c->spts64)
     }
 #undef HTS_WALK_ALL
+#undef HTS_WALK_GF
 #undef HTS_WALK
+    if (depth > 0) {
+        const int cb = (n + 255) / 256;
+        const int *fcount = reinterpret_cast<const int *>(reinterpret_cast<Frontier *>(c->split_frontier) +
+                                                          kMaxFrontier);
+        if (c->cfg.precision == HTS_FP32_MIXED)
+            walk_combine_kernel<PointF, float4><<<cb, 256, 0, c->stream>>>(
+                n, c->spts32, c->idx, reinterpret_cast<const float4 *>(c->split_part), fcount, c->frep, c->zi);
+        else
+            walk_combine_kernel<PointD, double4_32a><<<cb, 256, 0, c->stream>>>(
+                n, c->spts64, c->idx, reinterpret_cast<const double4_32a *>(c->split_part), fcount, c->frep,
+                c->zi);
+        c->launches += 1;
+    }
 }
+
+size_t walk_split_frontier_bytes() { return sizeof(Frontier) * kMaxFrontier + 64; }
 
 int exact_split(int64_t n)
 {

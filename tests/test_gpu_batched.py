@@ -157,6 +157,7 @@ def test_batched_equals_single_contexts_fp32():
         with HyperbolicTSNE(precision="fp32") as u:
             u.set_P(ip, ix, v)
             u.set_Y(y[off[s]:off[s + 1]])
+            u.set_walk_split(0)
             gs, _ = u.grad(0.5, 1.0)
         assert rel(g[off[s]:off[s + 1]], gs) < 1e-5
 
@@ -202,6 +203,7 @@ def test_steps_fp64_per_segment_learning_rates(theta):
                 with HyperbolicTSNE(precision="fp64") as u:
                     u.set_P(ip, ix, v)
                     u.set_Y(ys)
+                    u.set_walk_split(0)  # the batched walk is unsplit: same summation order
                     u.step(nst, theta, 12.0, sizes[s] / 12000.0, 0.5)
                     yu = u.get_Y()
                 assert rel(yg[off[s]:off[s + 1]], yu) < FP64_TOL
