@@ -281,7 +281,7 @@ HTS_API int hts_autotune(hts_ctx *ctx, double theta, int reps, int *tuning);
  * with an accepted ancestor is counted by one warp only, so every point gets
  * exactly the interactions of its own walk (the partial sums are added in a
  * fixed order).  depth = -1 (default) picks the shallowest cut that gives
- * about 2048 warps (8192 in HTS_FP64), within a partial-sum buffer of
+ * about 2048 warps, within a partial-sum buffer of
  * min(64 n, 2^22) entries for n <= 262144 (no split above).  Errors: HTS_EINVAL (depth < -1 or > 3). */
 HTS_API int hts_set_walk_split(hts_ctx *ctx, int depth);
 HTS_API int hts_set_tuning(hts_ctx *ctx, int walk_block, int attract_lanes);

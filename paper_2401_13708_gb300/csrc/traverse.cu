@@ -621,16 +621,18 @@ int walk_split_capacity(int64_t n)
     return (int)std::min<int64_t>(kMaxFrontier, kSplitEntries / n);
 }
 
-// Cut depth for n points: the shallowest that gives about 2048 warps (8192
-// for the float64 walk, whose long float64 latencies need more warps to
-// hide), within the buffer; `want` >= 0 overrides (clamped), -1 chooses.
+// Cut depth for n points: the shallowest that gives about 2048 warps, within
+// the buffer; `want` >= 0 overrides (clamped), -1 chooses.  (A deeper cut for
+// the float64 walk measured slower at N = 20,000: there the float64 pipe, not
+// the warp count, is the limit.)
 int walk_split_depth(int64_t n, int want, bool fp64)
 {
+    (void)fp64;
     const int cap = walk_split_capacity(n);
     int dmax = 0;
     while (dmax < kMaxSplitDepth && (1 << (2 * (dmax + 1))) <= cap) ++dmax;
     if (want >= 0) return std::min(want, dmax);
-    const int64_t chunks = (n + 31) / 32, target = fp64 ? 8192 : 2048;
+    const int64_t chunks = (n + 31) / 32, target = 2048;
     int d = 0;
     while (d < dmax && chunks * (1 << (2 * d)) < target) ++d;
     return d;
