@@ -424,10 +424,16 @@ def run_ours(args, rank, world, local):
                           "unit": "GB/s", "peak": hbm, "frac": agbs / hbm if hbm else None,
                           "note": "runs overlapped with the walk in the timed iteration"}
     wflop = flops / (sphase["walk"] * 1e-3) / 1e12
+    # special-function unit: rsqrt, log2 and reciprocal per interaction (3 ops)
+    mufu_tops = 3.0 * (acc + pairs) / K / (sphase["walk"] * 1e-3) / 1e12
+    mufu_peak = props.multi_processor_count * 16 * sm_mhz * 1e6 / 1e12
     kernels["walk"] = {"bound": "alu", "ms": sphase["walk"], "achieved": wflop, "unit": "TFLOP/s",
                        "peak": fp32_peak, "frac": wflop / fp32_peak,
                        "frac_of_measured_fp32": wflop / mpeaks["fp32_fma_tflops"]
-                       if mpeaks["fp32_fma_tflops"] else None}
+                       if mpeaks["fp32_fma_tflops"] else None,
+                       "mufu": {"achieved_tops": mufu_tops, "peak_tops": mufu_peak, "frac": mufu_tops / mufu_peak,
+                                "peak_basis": "SMs x 16 x sampled SM clock; measured: %.2f Tops/s" %
+                                              mpeaks["mufu_rsqrt_tops"]}}
 
     # ---- end to end through the C ABI, all iteration state in host memory -
     k_e2e = K  # the same iterations as the device-timed segment
