@@ -127,6 +127,14 @@ HTS_API int hts_set_P(hts_ctx *ctx, int64_t n, int64_t nnz, const int64_t *indpt
  * HTS_ECUDA. */
 HTS_API int hts_set_Y(hts_ctx *ctx, int64_t n, const double *y, int where);
 
+/* Overwrite the positions of the current Y (n x 2 float64, the n already
+ * set) and keep the optimiser state -- velocity, gains, iteration count --
+ * for a caller that holds Y in its own memory between steps or edits it
+ * (re-centring, constraints).  Checked on the device like hts_set_Y; returns
+ * once the copy is complete.  Errors: HTS_EINVAL, HTS_ENOTSET (no Y yet),
+ * HTS_EDOMAIN (then the context holds no Y), HTS_ECUDA. */
+HTS_API int hts_update_Y(hts_ctx *ctx, const double *y, int where);
+
 /* Run n_iter gradient-descent iterations (Sec. 5.1): each builds the tree
  * from the current Y, computes g = 4 (exaggeration * F_attr - F_rep / Z) with
  * the Barnes-Hut repulsion at `theta` (exact when theta == 0), and updates

@@ -124,6 +124,15 @@ class HyperbolicTSNE:
         self.n = n
         del keep
 
+    def update_Y(self, y):
+        """Overwrite the positions (same n) and keep velocity, gains and the
+        iteration count."""
+        if int(y.shape[0]) != self.n:
+            raise ValueError("update_Y keeps n; use set_Y for another size")
+        p, w, keep = _arg(y, np.float64)
+        self._check(self._lib.hts_update_Y(self._ctx, p, w))
+        del keep
+
     def set_cosne(self, lambda1: float = 1.0, lambda2: float = 0.0, x_sqnorm=None):
         """CO-SNE term (|x_i|^2 per point); x_sqnorm=None switches it off."""
         if x_sqnorm is None:

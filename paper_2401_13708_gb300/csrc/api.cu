@@ -683,6 +683,31 @@ int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
     return HTS_OK;
 }
 
+int hts_update_Y(hts_ctx *c, const double *y, int where)
+{
+    if (!c) return HTS_EINVAL;
+    c->err.clear();
+    if (!c->have_Y) return fail(c, HTS_ENOTSET, "hts_update_Y: set Y first");
+    if ((c->n > 0 && !y) || (where != HTS_HOST && where != HTS_DEVICE))
+        return fail(c, HTS_EINVAL, "hts_update_Y: invalid argument");
+    int r = set_device(c);
+    if (r) return r;
+    if (c->n == 0) return HTS_OK;
+    if (where == HTS_DEVICE && (r = check_device_ptr(c, y))) return r;
+    CK(cudaMemcpyAsync(c->y, y, sizeof(double2) * (size_t)c->n,
+                       where == HTS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    launch_check_y(c);
+    LAUNCHED("check_y");
+    int st = 0;
+    if ((r = read_status(c, &st))) return r;
+    if (st) {
+        c->have_Y = false;
+        return status_error(c, st);
+    }
+    return HTS_OK;
+}
+
 int hts_step(hts_ctx *c, int n_iter, double theta, double exaggeration, double lr, double momentum)
 {
     int r = ready(c);

@@ -88,11 +88,24 @@ struct UpdateArgs {
 
 __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
 {
+    __shared__ double s_invz;
     const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (!A.seg_of) {  // one problem: 1 / Z once per block (float64 division is costly here)
+        if (threadIdx.x == 0) {
+            const double Z0 = A.Z[0];
+            s_invz = Z0 > 0.0 ? 1.0 / Z0 : 0.0;
+        }
+        __syncthreads();
+    }
     if (i >= A.n) return;
     const int sg = A.seg_of ? A.seg_of[i] : 0;
-    const double Z = A.Z[sg];
-    const double invZ = Z > 0.0 ? 1.0 / Z : 0.0;
+    double invZ;
+    if (A.seg_of) {
+        const double Z = A.Z[sg];
+        invZ = Z > 0.0 ? 1.0 / Z : 0.0;
+    } else {
+        invZ = s_invz;
+    }
     const double2 fa = A.fattr[i], fr = A.frep[i];
     double gx = 4.0 * (A.exag * fa.x - fr.x * invZ);
     double gy = 4.0 * (A.exag * fa.y - fr.y * invZ);
@@ -137,9 +150,10 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
         q.x = (ca * p.x + a * ux) * rden;
         q.y = (ca * p.y + a * uy) * rden;
     }
-    const double r = sqrt(q.x * q.x + q.y * q.y);
-    if (r >= 1.0 - A.eps / 2.0) {
-        const double f = (1.0 - A.eps) / r;
+    const double q2 = q.x * q.x + q.y * q.y;
+    const double lim = 1.0 - A.eps / 2.0;
+    if (q2 >= lim * lim) {  // |q| >= 1 - eps/2 (Eq. HyperbolicProjection): back to radius 1 - eps
+        const double f = (1.0 - A.eps) / sqrt(q2);
         q.x *= f;
         q.y *= f;
     }

@@ -250,6 +250,25 @@ def test_degenerate_inputs(case, prec):
         t.close()
 
 
+def test_update_Y_keeps_optimiser_state():
+    w, y = workload("cfg1")
+    lr = w.n / 12000.0
+    with make("fp64", w, y) as t:
+        t.step(3, 0.5, 12.0, lr, 0.5)
+        t.step(2, 0.5, 12.0, lr, 0.5)
+        yb = t.get_Y()
+    with make("fp64", w, y) as u:
+        u.step(3, 0.5, 12.0, lr, 0.5)
+        u.update_Y(u.get_Y())                    # same positions: the run continues unchanged
+        u.step(2, 0.5, 12.0, lr, 0.5)
+        assert np.array_equal(u.get_Y(), yb)
+        _, _, it = u.get_state()
+        assert it == 5
+        from paper_2401_13708_gb300 import HtsError
+        with pytest.raises(HtsError, match="EDOMAIN"):
+            u.update_Y(np.full((w.n, 2), 0.8))   # |y| > 1
+
+
 def test_input_validation():
     from paper_2401_13708_gb300 import HtsError
     t = HyperbolicTSNE(precision="fp64")
