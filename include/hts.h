@@ -60,6 +60,8 @@ extern "C" {
 #define HTS_ECUDA (-5)    /* a CUDA runtime call failed (message has the CUDA error) */
 #define HTS_EOOM (-6)     /* device allocation failed */
 #define HTS_ENUMERIC (-7) /* device check tripped: non-finite gradient/position or tree overflow */
+#define HTS_ETIMEOUT (-9) /* a bounded device-side wait gave up (the results of that call are invalid;
+                             the context stays usable) */
 
 /* ---- enums ------------------------------------------------------------ */
 #define HTS_FP64 0        /* every step in float64 */

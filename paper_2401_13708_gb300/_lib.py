@@ -23,6 +23,7 @@ ERRORS = {
     -6: "HTS_EOOM",
     -7: "HTS_ENUMERIC",
     -8: "HTS_ETOOLARGE",
+    -9: "HTS_ETIMEOUT",
 }
 NOALLOC_MAX_N = 65536
 FP64, FP32_MIXED = 0, 1

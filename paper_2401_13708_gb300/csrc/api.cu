@@ -173,6 +173,7 @@ int read_status(hts_ctx *c, int *out)
 
 int status_error(hts_ctx *c, int st)
 {
+    if (st & 128) return fail(c, HTS_ETIMEOUT, "a bounded device-side wait (sort look-back) ran out");
     if (st & 64) return fail(c, HTS_EDOMAIN, "a point has |y| >= 1 or a non-finite coordinate");
     if (st & (8 | 16)) return fail(c, HTS_ESHAPE, "malformed CSR (indptr, indices or diagonal entries)");
     if (st & 32) return fail(c, HTS_EDOMAIN, "P has a negative or non-finite value");

@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
                     __nanosleep(64);
                     v = other.load(cuda::memory_order_relaxed);
                 }
-                if ((v >> 62) == 0ull) {  // gave up: report, and leave positions invalid
-                    atomicOr(status, 4);
+                if ((v >> 62) == 0ull) {  // gave up: report (HTS_ETIMEOUT), positions invalid
+                    atomicOr(status, 128);
                     excl = (long long)n;
                     break;
                 }

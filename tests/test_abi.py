@@ -42,3 +42,10 @@ def test_null_and_invalid_arguments_are_rejected_without_a_gpu():
     ctx = ctypes.c_void_p()
     assert lib.hts_create(ctypes.byref(ctx), ctypes.byref(cfg)) == -1
     assert lib.hts_step(None, 1, 0.5, 1.0, 1.0, 0.5) == -1
+
+
+def test_error_codes_match_the_header():
+    text = open(os.path.join(ROOT, "include", "hts.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"^#define (HTS_E\w+) \((-\d+)\)", text, flags=re.M)}
+    assert codes == _lib.ERRORS
+    assert re.search(r"^#define HTS_OK 0", text, flags=re.M)
