@@ -300,20 +300,6 @@ void launch_attract(hts_ctx *c)
     }
 }
 
-bool is_attract_kernel(const void *func)
-{
-    const void *k[] = {
-        (const void *)attract_f32_kernel<0, 4>,  (const void *)attract_f32_kernel<0, 8>,
-        (const void *)attract_f32_kernel<0, 16>, (const void *)attract_f32_kernel<0, 32>,
-        (const void *)attract_f32_kernel<1, 4>,  (const void *)attract_f32_kernel<1, 8>,
-        (const void *)attract_f32_kernel<1, 16>, (const void *)attract_f32_kernel<1, 32>,
-        (const void *)attract_f64_kernel<0>,     (const void *)attract_f64_kernel<1>,
-    };
-    for (const void *f : k)
-        if (f == func) return true;
-    return false;
-}
-
 void launch_kl_terms(hts_ctx *c)
 {
     const int n = (int)c->n;

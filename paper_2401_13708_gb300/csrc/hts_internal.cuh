@@ -204,7 +204,6 @@ void launch_kl_terms(hts_ctx *c);
 void launch_validate_csr(hts_ctx *c, int n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
                          const void *values, int f64);
 void launch_kl_rows(hts_ctx *c, double *a, double *b, double *p);
-bool is_attract_kernel(const void *func);  // one of the attraction kernels
 void launch_segments_setup(hts_ctx *c);
 // update.cu
 void launch_reduce_z(hts_ctx *c);
