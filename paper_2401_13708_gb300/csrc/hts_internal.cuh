@@ -10,7 +10,9 @@
 // Per point, key order:  keys / idx (uint64 / uint32, sort ping-pong),
 //   spts32 / spts64 (gathered records), terms (Einstein terms, 3 doubles).
 // Binary radix tree over the sorted keys (n - 1 internal nodes): children,
-//   parents, ranges, prefix lengths, arrival flags, double-double sums.
+//   parents, ranges, prefix lengths, per-point quad-level masks; exclusive
+//   prefix sums of the Einstein terms over the sorted points (3 x 128-bit
+//   fixed point, 48 B per point).
 // Polar quadtree (<= 2n - 1 nodes), pre-order with skip indices:
 //   NodeF (32 B) or NodeD (48 B).
 #pragma once
@@ -117,7 +119,7 @@ struct hts_ctx {
     // binary radix tree
     int *bn_left = nullptr, *bn_right = nullptr, *bn_parent = nullptr, *leaf_parent = nullptr;
     int *bn_lo = nullptr, *bn_hi = nullptr, *bn_pref = nullptr, *bn_flag = nullptr, *bn_quad = nullptr;
-    double *bn_sum = nullptr;  // 6 per node (double-double S_gamma, S_ux, S_uy)
+    double *bn_sum = nullptr;  // n + 1 prefix sums of S_gamma, S_ux, S_uy (3 x 128-bit fixed point)
     int *cnt = nullptr, *pre = nullptr;  // n + 1 each
 
     // quadtree
