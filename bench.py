@@ -54,7 +54,8 @@ def parse():
                     help="walk threads per block,attraction lanes per row (e.g. 256,8) instead of the autotuner")
     ap.add_argument("--suite", action="store_true",
                     help="per-workload report (all five configurations) instead of the headline line")
-    ap.add_argument("--configs", default="1,2,3,4,5", help="workloads of the --suite report")
+    ap.add_argument("--workloads", default="gaussian_mixture,mnist_like,binary_tree,batched_mixtures,single_cell",
+                    help="workloads of the --suite report")
     ap.add_argument("--profile-only", action="store_true",
                     help="FP32-mixed steps only (for a profiler): no FP64 arm, e2e or oracle")
     return ap.parse_args()
@@ -157,14 +158,14 @@ def workload(args, device):
     path = None
     if args.cache:
         os.makedirs(args.cache, exist_ok=True)
-        path = os.path.join(args.cache, f"cfg5_n{args.n}_s{args.seed}.npz")
+        path = os.path.join(args.cache, f"single_cell_n{args.n}_s{args.seed}.npz")
     if path and os.path.exists(path):
         z = np.load(path)
-        w = inputs.Workload(name=inputs.CONFIG_NAMES[5], n=int(z["indptr"].shape[0] - 1), indptr=z["indptr"],
+        w = inputs.Workload(name=inputs.WORKLOADS["single_cell"], n=int(z["indptr"].shape[0] - 1), indptr=z["indptr"],
                             indices=z["indices"], values=z["values"], y0=z["y0"], labels=z["labels"],
                             perplexity=30.0)
     else:
-        w = inputs.make_config(5, seed=args.seed, device=device, n=args.n)
+        w = inputs.make_workload("single_cell", seed=args.seed, device=device, n=args.n)
         if path:
             np.savez(path, indptr=w.indptr, indices=w.indices, values=w.values, y0=w.y0, labels=w.labels)
     y = inputs.spread_embedding(w.labels, args.seed)  # a harder, rim-heavy state for the error gate
@@ -623,13 +624,13 @@ def run_suite(args, rank, world, local):
         dt = (time.time() - t0) / k
         return {"s_per_iter": dt, "iters_per_s": 1.0 / dt, "iters_timed": k, "cores": cores, "cpu_model": model}
 
-    want = {int(v) for v in args.configs.split(",") if v.strip()}
+    want = {v.strip() for v in args.workloads.split(",") if v.strip()}
 
-    # config 1: N = 2000, FP64 CSR; 100 iterations, exaggeration 12 for 25, lr 1, momentum 0.5
-    w = inputs.make_config(1, seed=args.seed, device=dev)
+    # Gaussian mixture, N = 2000, FP64 CSR; 100 iterations, exaggeration 12 for 25, lr 1, momentum 0.5
+    w = inputs.make_workload("gaussian_mixture", seed=args.seed, device=dev)
     sched = schedule(100, 25, 12.0, 0.5, 0.5, 1.0)
-    for theta in ((0.0, 0.5) if 1 in want else ()):
-        line = {"workload": inputs.CONFIG_NAMES[1], "n": w.n, "nnz": w.nnz, "theta": theta,
+    for theta in ((0.0, 0.5) if "gaussian_mixture" in want else ()):
+        line = {"workload": inputs.WORKLOADS["gaussian_mixture"], "n": w.n, "nnz": w.nnz, "theta": theta,
                 "iterations": 100, "schedule": "25 x (exaggeration 12) + 75 x 1, lr 1, momentum 0.5"}
         line["fp64_gpu"] = gpu_time("fp64", w, w.y0, sched, theta, graphs=True)
         line["fp32_mixed_gpu"] = gpu_time("fp32", w, w.y0, sched, theta, graphs=True)
@@ -637,30 +638,30 @@ def run_suite(args, rank, world, local):
         line["oracle"] = oracle_iters(w, w.y0, 100, theta, 12.0, 1.0, 0.5)
         emit(line)
 
-    # configs 2, 3, 5: the paper's protocol, 1000 iterations, lr = N / 12000
-    for cfg, thetas in ((2, (0.5,)), (3, (0.2, 0.5, 0.8)), (5, (0.5, 0.8))):
-        if cfg not in want:
+    # MNIST-shaped, binary-tree and single-cell-like: the paper's protocol, 1000 iterations, lr = N / 12000
+    for name, thetas in (("mnist_like", (0.5,)), ("binary_tree", (0.2, 0.5, 0.8)), ("single_cell", (0.5, 0.8))):
+        if name not in want:
             continue
-        w = inputs.make_config(cfg, seed=args.seed, device=dev)
+        w = inputs.make_workload(name, seed=args.seed, device=dev)
         lr = w.n / 12000.0
         sched = schedule(1000, 250, 12.0, 0.5, 0.8, lr)
         for theta in thetas:
-            line = {"workload": inputs.CONFIG_NAMES[cfg], "n": w.n, "nnz": w.nnz, "theta": theta,
+            line = {"workload": inputs.WORKLOADS[name], "n": w.n, "nnz": w.nnz, "theta": theta,
                     "iterations": 1000,
                     "schedule": "250 x (exaggeration 12, momentum 0.5) + 750 x (1, 0.8), lr = N/12000"}
             line["fp32_mixed_gpu"] = gpu_time("fp32", w, w.y0, sched, theta)
-            f64 = gpu_time("fp64", w, w.y0, sched, theta, max_iters=60 if cfg == 5 else 250)
+            f64 = gpu_time("fp64", w, w.y0, sched, theta, max_iters=60 if name == "single_cell" else 250)
             line["fp64_gpu"] = f64
             f32p = gpu_time("fp32", w, w.y0, sched, theta, max_iters=f64["timed_iters"])
             line["fp32_mixed_speedup_over_fp64"] = {"iters": f64["timed_iters"],
                                                     "speedup": f32p["iters_per_s"] / f64["iters_per_s"]}
             if theta == 0.5:
-                k = 1 if cfg == 5 else 10
+                k = 1 if name == "single_cell" else 10
                 line["oracle"] = oracle_iters(w, w.y0, k, theta, 12.0, lr, 0.5)
             emit(line)
 
-    # config 4: 64 embeddings in one context, 500 iterations (125 exaggerated), lr = n_s / 12000
-    if 4 not in want:
+    # 64 mixtures in one context, 500 iterations (125 exaggerated), lr = n_s / 12000
+    if "batched_mixtures" not in want:
         return
     w = inputs.make_batched(64, seed=args.seed, device=dev)
     off = w.extra["offsets"]

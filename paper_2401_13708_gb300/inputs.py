@@ -46,9 +46,9 @@ __all__ = [
     "affinities_csr",
     "initial_embedding",
     "spread_embedding",
-    "make_config",
+    "make_workload",
     "make_batched",
-    "CONFIG_NAMES",
+    "WORKLOADS",
 ]
 
 
@@ -299,31 +299,32 @@ def spread_embedding(labels: np.ndarray, seed: int = 0, max_radius: float = 1 - 
 
 
 # ---------------------------------------------------------------------------
-# The five workloads
+# The named workloads
 # ---------------------------------------------------------------------------
 
-CONFIG_NAMES = {
-    1: "gaussian-mixture N=2000 D=50 (10 comps), FP64 CSR",
-    2: "mnist-like N=70000 D=784 -> PCA50, FP32 CSR",
-    3: "binary-tree diffusion N=131071 D=100 -> PCA50, FP32 CSR",
-    4: "64 batched mixtures N~logU(500,20000)",
-    5: "single-cell-like N=1000000 D=50 (200 Zipf clusters), FP32 CSR",
+WORKLOADS = {
+    "gaussian_mixture": "gaussian-mixture N=2000 D=50 (10 comps), FP64 CSR",
+    "mnist_like": "mnist-like N=70000 D=784 -> PCA50, FP32 CSR",
+    "binary_tree": "binary-tree diffusion N=131071 D=100 -> PCA50, FP32 CSR",
+    "batched_mixtures": "64 batched mixtures N~logU(500,20000)",
+    "single_cell": "single-cell-like N=1000000 D=50 (200 Zipf clusters), FP32 CSR",
 }
 
 
-def make_config(cfg: int, seed: int = 0, device: str = "cpu", n: Optional[int] = None,
-                perplexity: float = 30.0) -> Workload:
-    """Build workload `cfg` (1, 2, 3 or 5).  `n` overrides the size (tests)."""
-    if cfg == 1:
+def make_workload(name: str, seed: int = 0, device: str = "cpu", n: Optional[int] = None,
+                  perplexity: float = 30.0) -> Workload:
+    """Build a named workload (WORKLOADS; the batch has make_batched).  `n`
+    overrides the size (tests)."""
+    if name == "gaussian_mixture":
         nn = 2000 if n is None else n
         x, lab = gaussian_mixture(nn, 50, 10, seed)
         vdt = np.float64
-    elif cfg == 2:
+    elif name == "mnist_like":
         nn = 70000 if n is None else n
         x, lab = mnist_like(nn, 784, 10, seed)
         x = pca(x, 50, device)
         vdt = np.float32
-    elif cfg == 3:
+    elif name == "binary_tree":
         if n is None:
             x, lab = binary_tree_diffusion(16, 100, seed)
         else:
@@ -331,15 +332,15 @@ def make_config(cfg: int, seed: int = 0, device: str = "cpu", n: Optional[int] =
             x, lab = binary_tree_diffusion(depth, 100, seed)
         x = pca(x, 50, device)
         vdt = np.float32
-    elif cfg == 5:
+    elif name == "single_cell":
         nn = 1_000_000 if n is None else n
         x, lab = single_cell_like(nn, 50, 200 if nn >= 20000 else 20, seed)
         vdt = np.float32
     else:
-        raise ValueError("config must be 1, 2, 3 or 5 (4 is batched: batched_mixtures)")
+        raise ValueError(f"unknown workload {name!r} (the batch is make_batched)")
     indptr, indices, values = affinities_csr(x, perplexity, None, device, vdt)
     nn = int(indptr.shape[0] - 1)
-    return Workload(name=CONFIG_NAMES[cfg], n=nn, indptr=indptr, indices=indices, values=values,
+    return Workload(name=WORKLOADS[name], n=nn, indptr=indptr, indices=indices, values=values,
                     y0=initial_embedding(nn, seed), labels=lab, perplexity=perplexity)
 
 

@@ -25,13 +25,13 @@ ROWS = 2000
 _cache = {}
 
 
-def workload(cfg):
-    if cfg not in _cache:
+def workload(name):
+    if name not in _cache:
         import torch
         dev = "cuda" if torch.cuda.is_available() else "cpu"
-        w = inputs.make_config(cfg, seed=0, device=dev)
-        _cache[cfg] = (w, inputs.spread_embedding(w.labels, 0))
-    return _cache[cfg]
+        w = inputs.make_workload(name, seed=0, device=dev)
+        _cache[name] = (w, inputs.spread_embedding(w.labels, 0))
+    return _cache[name]
 
 
 def rel(a, b):
@@ -52,13 +52,13 @@ def gpu_grad(precision, w, y, theta):
         return t.grad(theta, 1.0)
 
 
-@pytest.mark.parametrize("cfg,theta,state", [
-    (2, 0.5, "y0"), (2, 0.5, "spread"),
-    (3, 0.2, "spread"), (3, 0.5, "spread"), (3, 0.8, "spread"),
-    (5, 0.5, "y0"), (5, 0.5, "spread"), (5, 0.8, "spread"),
+@pytest.mark.parametrize("name,theta,state", [
+    ("mnist_like", 0.5, "y0"), ("mnist_like", 0.5, "spread"),
+    ("binary_tree", 0.2, "spread"), ("binary_tree", 0.5, "spread"), ("binary_tree", 0.8, "spread"),
+    ("single_cell", 0.5, "y0"), ("single_cell", 0.5, "spread"), ("single_cell", 0.8, "spread"),
 ])
-def test_fullsize_fp32_sampled_rows(cfg, theta, state):
-    w, spread = workload(cfg)
+def test_fullsize_fp32_sampled_rows(name, theta, state):
+    w, spread = workload(name)
     y = w.y0 if state == "y0" else spread
     rows = rows_for(w.n)
     ref = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=theta, exag=1.0, rows=rows)
@@ -67,9 +67,9 @@ def test_fullsize_fp32_sampled_rows(cfg, theta, state):
     assert rel(g[rows], ref["g"]) < FP32_TOL
 
 
-@pytest.mark.parametrize("cfg,theta", [(3, 0.2), (3, 0.8), (5, 0.5)])
-def test_fullsize_fp64_sampled_rows(cfg, theta):
-    w, spread = workload(cfg)
+@pytest.mark.parametrize("name,theta", [("binary_tree", 0.2), ("binary_tree", 0.8), ("single_cell", 0.5)])
+def test_fullsize_fp64_sampled_rows(name, theta):
+    w, spread = workload(name)
     rows = rows_for(w.n, seed=11)
     ref = oracle.bh_grad(spread, w.indptr, w.indices, w.values, theta=theta, exag=1.0, rows=rows)
     g, Z = gpu_grad("fp64", w, spread, theta)

@@ -45,20 +45,20 @@ _cache = {}
 def workload(name):
     if name in _cache:
         return _cache[name]
-    if name == "cfg1":
-        w = inputs.make_config(1, seed=0)
+    if name == "mixture":
+        w = inputs.make_workload("gaussian_mixture", seed=0)
         y = inputs.spread_embedding(w.labels, 0, rho_hi=8.0)
-    elif name == "cfg1_init":
-        w = inputs.make_config(1, seed=0)
+    elif name == "mixture_init":
+        w = inputs.make_workload("gaussian_mixture", seed=0)
         y = w.y0
     elif name == "ragged":
-        w = inputs.make_config(1, seed=4, n=4097)
+        w = inputs.make_workload("gaussian_mixture", seed=4, n=4097)
         y = inputs.spread_embedding(w.labels, 4)
-    elif name == "cfg3_small":
-        w = inputs.make_config(3, seed=0, n=8191)
+    elif name == "tree_small":
+        w = inputs.make_workload("binary_tree", seed=0, n=8191)
         y = inputs.spread_embedding(w.labels, 1, rho_hi=10.0)
-    elif name == "cfg2_small":
-        w = inputs.make_config(2, seed=0, n=12000)
+    elif name == "mnist_small":
+        w = inputs.make_workload("mnist_like", seed=0, n=12000)
         y = inputs.spread_embedding(w.labels, 2, rho_hi=12.0)
     else:
         raise KeyError(name)
@@ -66,7 +66,7 @@ def workload(name):
     return w, y
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg1_init", "ragged"])
+@pytest.mark.parametrize("name", ["mixture", "mixture_init", "ragged"])
 @pytest.mark.parametrize("rule", [0, 1])
 def test_keys_bit_exact(name, rule):
     w, y = workload(name)
@@ -77,7 +77,7 @@ def test_keys_bit_exact(name, rule):
     assert np.array_equal(k, ko)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg1_init", "ragged", "cfg3_small"])
+@pytest.mark.parametrize("name", ["mixture", "mixture_init", "ragged", "tree_small"])
 @pytest.mark.parametrize("rule", [0, 1])
 def test_tree_matches_oracle(name, rule):
     w, y = workload(name)
@@ -93,7 +93,7 @@ def test_tree_matches_oracle(name, rule):
     assert np.allclose(g["rcell"][fin], o["rcell"][fin], rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg1_init", "ragged"])
+@pytest.mark.parametrize("name", ["mixture", "mixture_init", "ragged"])
 def test_exact_fp64(name):
     w, y = workload(name)
     ref = oracle.exact_grad(y, w.indptr, w.indices, w.values, exag=12.0)
@@ -104,7 +104,7 @@ def test_exact_fp64(name):
     assert maxrel(g, ref["g"]) < FP64_TOL
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg1_init", "ragged", "cfg3_small"])
+@pytest.mark.parametrize("name", ["mixture", "mixture_init", "ragged", "tree_small"])
 @pytest.mark.parametrize("theta", [0.2, 0.5, 0.8])
 def test_bh_fp64(name, theta):
     w, y = workload(name)
@@ -116,7 +116,7 @@ def test_bh_fp64(name, theta):
     assert maxrel(g, ref["g"]) < FP64_TOL
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg1_init", "ragged", "cfg3_small", "cfg2_small"])
+@pytest.mark.parametrize("name", ["mixture", "mixture_init", "ragged", "tree_small", "mnist_small"])
 @pytest.mark.parametrize("theta", [0.5, 0.8])
 def test_bh_fp32_mixed(name, theta):
     w, y = workload(name)
@@ -127,7 +127,7 @@ def test_bh_fp32_mixed(name, theta):
     assert rel(g, ref["g"]) < FP32_TOL
 
 
-@pytest.mark.parametrize("name", ["cfg1", "ragged"])
+@pytest.mark.parametrize("name", ["mixture", "ragged"])
 def test_exact_fp32_mixed(name):
     w, y = workload(name)
     ref = oracle.exact_grad(y, w.indptr, w.indices, w.values, exag=12.0)
@@ -139,7 +139,7 @@ def test_exact_fp32_mixed(name):
 
 @pytest.mark.parametrize("theta", [0.0, 0.5])
 def test_steps_fp64_track_oracle(theta):
-    w, y = workload("cfg1")
+    w, y = workload("mixture")
     lr = w.n / 12000.0
     yo, vo, _ = oracle.step(y, np.zeros_like(y), w.indptr, w.indices, w.values, 10, theta, 12.0, lr, 0.5)
     with make("fp64", w, y) as t:
@@ -152,7 +152,7 @@ def test_steps_fp64_track_oracle(theta):
 
 
 def test_steps_with_gains_and_metric2():
-    w, y = workload("cfg1_init")
+    w, y = workload("mixture_init")
     gains = np.ones_like(y)
     yo, vo, go = oracle.step(y, np.zeros_like(y), w.indptr, w.indices, w.values, 5, 0.5, 12.0, 1.0, 0.5,
                              gains=gains, metric_pow=2)
@@ -166,7 +166,7 @@ def test_steps_with_gains_and_metric2():
 
 @pytest.mark.parametrize("theta", [0.0, 0.5])
 def test_kl(theta):
-    w, y = workload("cfg1")
+    w, y = workload("mixture")
     ref = oracle.kl(y, w.indptr, w.indices, w.values, theta=theta)
     with make("fp64", w, y) as t:
         assert t.kl(theta) == pytest.approx(ref, rel=1e-10)
@@ -175,7 +175,7 @@ def test_kl(theta):
 
 
 def test_paper_printed_gradient_form():
-    w, y = workload("cfg1")
+    w, y = workload("mixture")
     ref = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=0.5, grad_form=1)
     with make("fp64", w, y, grad_form="paper") as t:
         g, _ = t.grad(0.5, 1.0)
@@ -251,7 +251,7 @@ def test_degenerate_inputs(case, prec):
 
 
 def test_update_Y_keeps_optimiser_state():
-    w, y = workload("cfg1")
+    w, y = workload("mixture")
     lr = w.n / 12000.0
     with make("fp64", w, y) as t:
         t.step(3, 0.5, 12.0, lr, 0.5)

@@ -20,7 +20,7 @@ _cache = {}
 
 def problem(n):
     if n not in _cache:
-        w = inputs.make_config(1, seed=2, n=n)
+        w = inputs.make_workload("gaussian_mixture", seed=2, n=n)
         _cache[n] = (w, inputs.spread_embedding(w.labels, 3, rho_hi=9.0))
     return _cache[n]
 

@@ -19,7 +19,7 @@ _w = {}
 
 def problem():
     if "w" not in _w:
-        w = inputs.make_config(1, seed=5, n=3001)
+        w = inputs.make_workload("gaussian_mixture", seed=5, n=3001)
         _w["w"] = (w, inputs.spread_embedding(w.labels, 5, rho_hi=9.0))
     return _w["w"]
 

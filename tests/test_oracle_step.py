@@ -15,7 +15,7 @@ from paper_2401_13708_gb300 import inputs
 
 
 def problem(n=300, seed=0):
-    w = inputs.make_config(1, seed=seed, n=n)
+    w = inputs.make_workload("gaussian_mixture", seed=seed, n=n)
     y = inputs.spread_embedding(w.labels, seed, rho_hi=5.0)
     return w, y
 

@@ -298,7 +298,7 @@ def test_bh_matches_pure_python_literal_algorithm(theta):
 
 
 def _config1_small(n=1500):
-    w = inputs.make_config(1, seed=0, n=n)
+    w = inputs.make_workload("gaussian_mixture", seed=0, n=n)
     y = inputs.spread_embedding(w.labels, 0, rho_hi=6.0)
     return w, y
 

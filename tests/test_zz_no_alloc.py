@@ -35,7 +35,7 @@ def test_noalloc_matches_exact_gradient_twice():
     stream = torch.cuda.current_stream()
     cases = []
     for seed, n in ((0, 2000), (1, 3001)):
-        w = inputs.make_config(1, seed=seed, n=n)
+        w = inputs.make_workload("gaussian_mixture", seed=seed, n=n)
         y = inputs.spread_embedding(w.labels, seed, rho_hi=8.0)
         with HyperbolicTSNE(precision="fp64") as t:
             t.set_P(w.indptr, w.indices, w.values)
