@@ -197,7 +197,9 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
 {
 #define MARK(k) \
     if (ev) CK(cudaEventRecord(ev[k], c->stream))
-    const bool serial = c->profiling == 2;  // every phase alone (timing)
+    // every phase alone (timing), and the exact path: its kernel fills the GPU
+    // by itself, and an attraction beside it only lengthens its tail
+    const bool serial = c->profiling == 2 || theta == 0.0;
     const bool attract = c->nnz > 0 && !serial;
     // fork: the side stream waits for the point records (and for the stages
     // before kAttractAfter, so that it does not hold SMs they need)
@@ -220,7 +222,6 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
     LAUNCHED("prep_points");
     if (c->nnz == 0) CK(cudaMemsetAsync(c->fattr, 0, sizeof(double2) * (size_t)c->n, c->stream));
     if (theta == 0.0) {
-        if (attract && (r = fork_attract())) return r;
         MARK(1);
         MARK(2);
         MARK(3);
