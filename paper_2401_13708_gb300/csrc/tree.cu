@@ -426,9 +426,22 @@ __global__ void emit_kernel(EmitArgs A)
         const double sg = fx_to_double(p1.g - p0.g, E);
         const double sux = fx_to_double(p1.x - p0.x, E);
         const double suy = fx_to_double(p1.y - p0.y, E);
-        double mx = __ddiv_rn(sux, sg), my = __ddiv_rn(suy, sg);
-        double sq = __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))));
-        double cx = __ddiv_rn(mx, __dadd_rn(1.0, sq)), cy = __ddiv_rn(my, __dadd_rn(1.0, sq));
+        double mx, my, sq, cx, cy;
+        if (A.nodes64 || A.ex.depth) {  // float64 walk / export: the oracle's correctly rounded steps
+            mx = __ddiv_rn(sux, sg);
+            my = __ddiv_rn(suy, sg);
+            sq = __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))));
+            cx = __ddiv_rn(mx, __dadd_rn(1.0, sq));
+            cy = __ddiv_rn(my, __dadd_rn(1.0, sq));
+        } else {  // float32 nodes: two reciprocals instead of four divisions
+            const double rs = 1.0 / sg;
+            mx = sux * rs;
+            my = suy * rs;
+            sq = sqrt(1.0 - (mx * mx + my * my));
+            const double rd = 1.0 / (1.0 + sq);
+            cx = mx * rd;
+            cy = my * rd;
+        }
         double beta = __dsub_rn(1.0, __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)));
         double il = 1.0 / beta;
         const uint64_t key = A.keys[lo];
