@@ -172,6 +172,12 @@ def workload(args, device):
     return w, y, time.time() - t0
 
 
+def workload_name(n, theta):
+    """The headline workload, as both arms name it."""
+    return (f"single-cell-like N={n} D=50 (200 Zipf clusters, log-normal), kNN k=90 perplexity 30, FP32 CSR, "
+            f"theta={theta}, paper protocol from Y0")
+
+
 def oracle_pass(w, y, theta, rows):
     """One oracle BH pass: full tree + all n walks (for Z) + gradient rows."""
     import oracle
@@ -218,7 +224,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"single-cell-like N={n} D=50, kNN k=90 perplexity 30, theta={args.theta}",
+            "config": {"workload": workload_name(n, args.theta),
                        "n": n, "nnz": w.nnz, "theta": args.theta},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -515,8 +521,7 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"single-cell-like N={n} D=50 (200 Zipf clusters, log-normal), kNN k=90 perplexity "
-                               f"30, FP32 CSR, theta={theta}, FP32-mixed, paper protocol from Y0", "n": n,
+        "config": {"workload": workload_name(n, theta), "n": n,
                    "nnz": int(w.nnz), "theta": theta, "precision": "fp32_mixed",
                    "protocol": f"iterations {W}..{W + K - 1} of 250 (exaggeration 12, momentum 0.5) + 750 "
                                f"(1, 0.8), lr = N/12000, Y0 ~ N(0, 1e-4 I)",
