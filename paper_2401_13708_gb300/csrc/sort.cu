@@ -270,15 +270,18 @@ namespace {
 
 // n <= kTile: all eight passes in one block (no look-back: the block's own
 // histogram is the global one), ping-ponging through the two key buffers.
+// ROUNDS keys per lane: 256 * ROUNDS >= n (fewer rounds for fewer keys).
+template <int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads) small_sort_kernel(uint64_t *ka, uint32_t *va, uint64_t *kb,
                                                                   uint32_t *vb, int n)
 {
+    constexpr int kRounds = ROUNDS;
     __shared__ int wh[kWarps][256];
     __shared__ int dsum[256];
     __shared__ int wtot[kWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int base = w * kPerWarp;
+    const int base = w * 32 * ROUNDS;
     for (int p = 0; p < kPasses; ++p) {
         const uint64_t *kin = (p & 1) ? kb : ka;
         const uint32_t *vin = (p & 1) ? vb : va;
@@ -361,7 +364,13 @@ void launch_sort_pairs(hts_ctx *c)
     const int n = (int)c->n;
     const int tiles = (n + kTile - 1) / kTile;
     if (tiles == 1) {  // one block does all eight passes
-        small_sort_kernel<<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt, n);
+        if (n <= kSortThreads * 4)
+            small_sort_kernel<4><<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt, n);
+        else if (n <= kSortThreads * 8)
+            small_sort_kernel<8><<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt, n);
+        else
+            small_sort_kernel<kRounds><<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt,
+                                                                          n);
         c->launches += 1;
         return;
     }
