@@ -184,12 +184,13 @@ int status_error(hts_ctx *c, int st)
 
 constexpr int kPhases = 6;  // keys, sort, tree, walk/exact, attract, Z + update
 constexpr int kEvents = kPhases + 3;  // per iteration: 6 marks on the main stream, 2 on the side stream
-constexpr int kAttractAfter = 0;      // stage after which the attraction forks: 0 prep, 1 keys, 2 sort, 3 tree
+constexpr int kAttractAfter = 3;      // stage after which the attraction forks: 0 prep, 1 keys, 2 sort, 3 tree
 
 // Repulsion, attraction and Z for the current Y (results in frep, zi, fattr,
 // dscal[0] / seg_z).  The attractive sum needs only the point records, so it
 // runs on the side stream (lowest priority) from the stage kAttractAfter to
-// the Z reduction, overlapping the key / sort / tree / walk kernels.  With `ev` (kEvents events)
+// the Z reduction, as a small resident grid beside the walk (see
+// launch_attract).  With `ev` (kEvents events)
 // the stage boundaries are recorded: ev[0..4] and ev[6] on the main stream
 // (start, after keys, sort, tree, walk / exact; ev[6] after the update is
 // recorded by the caller), ev[7..8] around the attractive sum.
@@ -209,7 +210,9 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
         cudaStream_t keep = c->stream;
         c->stream = c->astream;
         if (ev) CK(cudaEventRecord(ev[7], c->astream));
+        c->attract_background = 1;
         launch_attract(c);
+        c->attract_background = 0;
         c->stream = keep;
         LAUNCHED("attract");
         if (ev) CK(cudaEventRecord(ev[8], c->astream));

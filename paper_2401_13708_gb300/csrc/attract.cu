@@ -9,6 +9,8 @@
 // Per point: F_attr,i = 4 il_i (A_Delta + il_i A_s y_i) with
 //   A_Delta = sum_j p_ij (w d / t)_ij il_j Delta_ij,  A_s = same with s_ij.
 // Bytes per non-zero: 4 (index) + 4 or 8 (value) + 32 (gathered record).
+#include <algorithm>
+
 #include "hts_internal.cuh"
 
 namespace hts {
@@ -21,6 +23,7 @@ constexpr int kBlock = 256;
 // leave most of a warp idle; each lane keeps kUnroll index loads and gathers
 // in flight before its arithmetic.
 constexpr int kUnroll = 4;
+constexpr int kAttractBlocksPerSM = 8;  // launch beside the walk: resident blocks per SM (0: full grid)
 
 template <int GF, int kGroup>
 __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_t *__restrict__ indptr,
@@ -28,7 +31,11 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
                                                              const float *__restrict__ vals,
                                                              const PointF *__restrict__ pts, double2 *fattr)
 {
-    const int row = (blockIdx.x * kBlock + threadIdx.x) / kGroup;
+    // grid-stride over blocks of rows: one pass with the full grid, several
+    // with the small grid of the background launch (kAttractBlocksPerSM)
+    const int64_t span = (int64_t)n * kGroup;
+    for (int64_t base = (int64_t)blockIdx.x * kBlock; base < span; base += (int64_t)gridDim.x * kBlock) {
+    const int row = (int)((base + threadIdx.x) / kGroup);
     const int lane = threadIdx.x & (kGroup - 1);
     const bool live = row < n;
     const int r = live ? row : n - 1;
@@ -71,6 +78,7 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
         double il = (double)q.il;
         double asd = il * (double)as;
         fattr[row] = make_double2(4.0 * il * ((double)ax + asd * x), 4.0 * il * ((double)ay + asd * y));
+    }
     }
 }
 
@@ -270,7 +278,12 @@ void launch_attract(hts_ctx *c)
     const int n = (int)c->n;
     const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
     const int G = c->attract_group;
-    const int blocks32 = (int)(((int64_t)n * G + kBlock - 1) / kBlock);
+    // kAttractBlocksPerSM > 0: a small resident grid that strides over the rows
+    // in the background of the walk instead of one block per 256 / G rows
+    const int full = (int)(((int64_t)n * G + kBlock - 1) / kBlock);
+    const int blocks32 = kAttractBlocksPerSM > 0 && c->attract_background
+                             ? std::min(full, kAttractBlocksPerSM * c->sm_count)
+                             : full;
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
         const float *v = (const float *)c->values;

@@ -160,6 +160,7 @@ struct hts_ctx {
     int walk_block = 256;            // walk threads per block: 32, 64, 128 or 256
     int attract_group = 8;           // float32 attraction lanes per row of P: 4, 8, 16 or 32
     int walk_split = -1;             // cut depth of the split walk (-1: by problem size)
+    int attract_background = 0;      // set while the attraction is launched beside the walk
     void *split_frontier = nullptr;  // frontier table + entry count
     void *split_part = nullptr;      // partial sums of the split walk
 
