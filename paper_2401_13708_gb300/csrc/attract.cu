@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(kBlock) attract_f64_kernel(int n, const int64_
                                                              const double *__restrict__ vals,
                                                              const PointD *__restrict__ pts, double2 *fattr)
 {
-    const int row = (blockIdx.x * kBlock + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (row >= n) return;
+    // grid-stride over rows (a warp per row), as in the float32 kernel
+    for (int row = (blockIdx.x * kBlock + threadIdx.x) >> 5; row < n; row += (gridDim.x * kBlock) >> 5) {
     const PointD q = pts[row];
     const double twoil = 2.0 * q.il;
     const int64_t e0 = indptr[row], e1 = indptr[row + 1];
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kBlock) attract_f64_kernel(int n, const int64_
     if (lane == 0) {
         double asd = q.il * as;
         fattr[row] = make_double2(4.0 * q.il * (ax + asd * q.x), 4.0 * q.il * (ay + asd * q.y));
+    }
     }
 }
 
@@ -284,6 +285,9 @@ void launch_attract(hts_ctx *c)
     const int blocks32 = kAttractBlocksPerSM > 0 && c->attract_background
                              ? std::min(full, kAttractBlocksPerSM * c->sm_count)
                              : full;
+    const int blocks64 = kAttractBlocksPerSM > 0 && c->attract_background
+                             ? std::min(blocks, kAttractBlocksPerSM * c->sm_count)
+                             : blocks;
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
         const float *v = (const float *)c->values;
@@ -307,9 +311,11 @@ void launch_attract(hts_ctx *c)
     } else {
         const double *v = (const double *)c->values;
         if (c->cfg.grad_form == HTS_EXACT_KL)
-            attract_f64_kernel<0><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts64, c->fattr);
+            attract_f64_kernel<0><<<blocks64, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts64,
+                                                                      c->fattr);
         else
-            attract_f64_kernel<1><<<blocks, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts64, c->fattr);
+            attract_f64_kernel<1><<<blocks64, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts64,
+                                                                      c->fattr);
     }
 }
 
