@@ -41,17 +41,20 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
     const int r = live ? row : n - 1;
     const PointF q = pts[r];
     const float twoil = 2.0f * q.il;
-    const int64_t e0 = indptr[r], e1 = live ? indptr[r + 1] : e0;
+    const int64_t e0 = indptr[r];
+    const int len = live ? (int)(indptr[r + 1] - e0) : 0;  // a row is shorter than 2^31
+    const int32_t *__restrict__ ir = indices + e0;
+    const float *__restrict__ vr = vals + e0;
     float ax = 0.f, ay = 0.f, as = 0.f;
-    for (int64_t e = e0 + lane; e < e1; e += kGroup * kUnroll) {
+    for (int e = lane; e < len; e += kGroup * kUnroll) {
         int j[kUnroll];
         float pv[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const int64_t eu = e + kGroup * u;
-            const bool ok = eu < e1;
-            j[u] = ok ? __ldg(indices + eu) : r;
-            pv[u] = ok ? __ldg(vals + eu) : 0.0f;
+            const int eu = e + kGroup * u;
+            const bool ok = eu < len;
+            j[u] = ok ? __ldg(ir + eu) : r;
+            pv[u] = ok ? __ldg(vr + eu) : 0.0f;
         }
         PointF o[kUnroll];
 #pragma unroll
