@@ -44,7 +44,8 @@ struct __align__(16) PointD {
     double x, y, il, pad;
 };
 
-// Tree node, float32 mode (one 32-byte sector).
+// Tree node, float32 mode (one 32-byte sector; count is a float holding an
+// integer, so the walk multiplies by it without a conversion).
 //   count >= 2 : internal cell; (xh, yh, xl, yl) Einstein midpoint, il of the
 //                midpoint, thr = cosh(r_cell / theta) - 1 (accept iff the
 //                pair's delta = cosh(d) - 1 exceeds it), skip = pre-order
@@ -56,7 +57,8 @@ struct __align__(16) PointD {
 struct __align__(16) NodeF {
     float xh, yh, xl, yl;
     float il, thr;
-    int count, skip;
+    float count;
+    int skip;
 };
 
 // Tree node, float64 mode (same meaning; pos = sorted position for leaves

@@ -45,7 +45,7 @@ __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int 
     r.yl = a.w;
     r.il = b.x;
     r.thr = b.y;
-    r.count = __float_as_int(b.z);
+    r.count = b.z;
     r.skip = __float_as_int(b.w);
     return r;
 }
@@ -186,7 +186,7 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
                 if (COUNT) ++c_pair;
             }
         } else {
-            const int lo = __float_as_int(c.thr), cnt = -c.count;
+            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
             if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
                 for (int k2 = 0; k2 < cnt; ++k2) {
                     if (lo + k2 == p) continue;
@@ -246,7 +246,7 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
                 if (COUNT) ++c_pair;
             }
         } else {
-            const int lo = __float_as_int(c.thr), cnt = -c.count;
+            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
             if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
                 for (int k2 = 0; k2 < cnt; ++k2) {
                     if (lo + k2 == p) continue;
@@ -306,7 +306,7 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
                 if (COUNT) ++c_pair;
             }
         } else {
-            const int lo = __float_as_int(c.thr), cnt = -c.count;
+            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
             if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
                 for (int k2 = 0; k2 < cnt; ++k2) {
                     if (lo + k2 == p) continue;
@@ -366,7 +366,7 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
                 if (COUNT) ++c_pair;
             }
         } else {
-            const int lo = __float_as_int(c.thr), cnt = -c.count;
+            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
             if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
                 for (int k2 = 0; k2 < cnt; ++k2) {
                     if (lo + k2 == p) continue;
@@ -591,7 +591,7 @@ __global__ void frontier_kernel(const NT *__restrict__ nodes, const int *__restr
         for (int e = 0; e < na && !bad; ++e) {
             const Frontier &E = a[e];
             const NT c = nodes[E.node];
-            const int cnt = c.count & 0x7fffffff;
+            const int cnt = (int)c.count;
             if (c.count < 2 || cnt < 2) {  // leaf or bucket: stays an entry
                 if (nb >= kMaxFrontier) { bad = true; break; }
                 b[nb++] = E;
