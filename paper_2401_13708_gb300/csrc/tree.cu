@@ -51,9 +51,11 @@ constexpr int kBlock = 256;
 // Sorted point records and the Einstein terms; *gmax receives the largest
 // gamma (bits of a positive double order like the double), which bounds every
 // term (|gamma v| <= gamma).
+// exact: the oracle's correctly rounded divisions (float64 nodes, exports);
+// otherwise one reciprocal (the float32 nodes round the result to float).
 __global__ void gather_kernel(int n, const uint32_t *__restrict__ idx, const double2 *__restrict__ y,
                               const PointF *__restrict__ pts32, const PointD *__restrict__ pts64, PointF *spts32,
-                              PointD *spts64, double *terms, unsigned long long *gmax)
+                              PointD *spts64, double *terms, unsigned long long *gmax, int exact)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long gb = 0;
@@ -64,10 +66,18 @@ __global__ void gather_kernel(int n, const uint32_t *__restrict__ idx, const dou
         double2 q = y[i];
         double n2 = __dadd_rn(__dmul_rn(q.x, q.x), __dmul_rn(q.y, q.y));
         double a = __dsub_rn(1.0, n2);
-        const double g = __ddiv_rn(__dadd_rn(1.0, n2), a);
+        double g;
+        if (exact) {
+            g = __ddiv_rn(__dadd_rn(1.0, n2), a);
+            terms[3 * p + 1] = __ddiv_rn(__dmul_rn(2.0, q.x), a);
+            terms[3 * p + 2] = __ddiv_rn(__dmul_rn(2.0, q.y), a);
+        } else {
+            const double ia = 1.0 / a;
+            g = (1.0 + n2) * ia;
+            terms[3 * p + 1] = 2.0 * q.x * ia;
+            terms[3 * p + 2] = 2.0 * q.y * ia;
+        }
         terms[3 * p + 0] = g;
-        terms[3 * p + 1] = __ddiv_rn(__dmul_rn(2.0, q.x), a);
-        terms[3 * p + 2] = __ddiv_rn(__dmul_rn(2.0, q.y), a);
         gb = (unsigned long long)__double_as_longlong(g);
     }
     for (int o = 16; o > 0; o >>= 1) gb = max(gb, __shfl_xor_sync(0xffffffffu, gb, o));
@@ -569,7 +579,7 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex)
     unsigned long long *gmax = c->minmax + 2 * kMaxSegments;
     cudaMemsetAsync(gmax, 0, sizeof(unsigned long long), s);
     gather_kernel<<<gp, kBlock, 0, s>>>(n, c->idx, c->y, c->pts32, c->pts64, f32 ? c->spts32 : nullptr,
-                                        f32 ? nullptr : c->spts64, c->terms, gmax);
+                                        f32 ? nullptr : c->spts64, c->terms, gmax, (!f32 || ex) ? 1 : 0);
     c->launches += 4;  // gather, quad_mark, count, emit
     FX3 *prefix = reinterpret_cast<FX3 *>(c->bn_sum);  // n + 1 entries
     unsigned *mask = reinterpret_cast<unsigned *>(c->bn_flag);
