@@ -137,11 +137,13 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
     const double lr = A.seg_of ? A.lr * A.seg_lr[sg] : A.lr;
     v.x = A.mom * v.x - lr * kx * (gx * sc);
     v.y = A.mom * v.y - lr * ky * (gy * sc);
-    const double nv = sqrt(v.x * v.x + v.y * v.y);
+    const double vv = v.x * v.x + v.y * v.y;
     double2 q = p;
-    if (nv > 0.0) {
-        // exp map: p (+) tanh(lambda |v| / 2) v / |v|, lambda |v| / 2 = |v| / a
-        const double f = tanh(nv / a) / nv;
+    if (vv > 0.0) {
+        // exp map: p (+) tanh(lambda |v| / 2) v / |v|, lambda |v| / 2 = |v| / a;
+        // 1 / |v| from one reciprocal square root (no square root and division)
+        const double rn = rsqrt(vv), nv = vv * rn;
+        const double f = tanh(nv / a) * rn;
         const double ux = f * v.x, uy = f * v.y;
         const double pu = p.x * ux + p.y * uy;
         const double nu = ux * ux + uy * uy;

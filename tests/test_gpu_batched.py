@@ -277,3 +277,21 @@ def test_graph_replay_is_bit_identical(segmented):
             t.step(3, 0.5, 1.0, lr, 0.8)  # the cached one
             out.append(t.get_Y())
     assert np.array_equal(out[0], out[1])
+
+
+def test_cosne_term_per_segment():
+    """With segments the CO-SNE term of each point uses its segment's size."""
+    w, y = batch()
+    off = w.extra["offsets"]
+    rng = np.random.default_rng(5)
+    xsq = rng.uniform(0.0, 4.0, size=w.n)
+    l1, l2 = 0.7, 0.05
+    with batched_ctx("fp64", w, y) as t:
+        t.set_cosne(l1, l2, xsq)
+        g, _ = t.grad(0.5, 1.0)
+    for s in range(len(off) - 1):
+        a, b = int(off[s]), int(off[s + 1])
+        ip, ix, v = block(w, s)
+        gk = oracle.bh_grad(y[a:b], ip, ix, v, theta=0.5, exag=1.0)["g"]
+        ref = oracle.cosne_grad(y[a:b], xsq[a:b], l1, l2, gk)
+        assert rel(g[a:b], ref) < FP64_TOL
