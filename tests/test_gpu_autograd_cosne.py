@@ -34,7 +34,7 @@ def test_klfunction_gradcheck_and_oracle():
     model.set_P(ip, ix, vv)
     yt = torch.tensor(y, dtype=torch.float64, device="cuda", requires_grad=True)
     loss = kl_divergence(yt, model, 0.0)
-    assert float(loss) == pytest.approx(oracle.kl(y, ip, ix, vv, 0.0), rel=1e-10)
+    assert float(loss.detach()) == pytest.approx(oracle.kl(y, ip, ix, vv, 0.0), rel=1e-10)
     loss.backward()
     ref = oracle.exact_grad(y, ip, ix, vv)["g"]
     g = yt.grad.cpu().numpy()
