@@ -275,7 +275,8 @@ HTS_API int hts_set_graphs(hts_ctx *ctx, int enable);
  * times `reps` launches of every candidate of each kernel on the context's
  * stream with CUDA events, keeps the fastest and writes the choice to
  * tuning[2] = {walk threads per block, attraction lanes per row} (may be
- * NULL).  It changes no result of the walk (the work split per warp does not
+ * NULL); for a small problem it also picks the split walk's cut depth
+ * (hts_get_walk_split).  It changes no result of the walk (the work split per warp does not
  * depend on the block size); lanes per row change only the float32 summation
  * order inside a row.  hts_set_tuning sets them directly (0 keeps a value),
  * hts_get_tuning reads them.  Defaults: {256, 8}.  Errors: HTS_ENOTSET,
@@ -294,6 +295,10 @@ HTS_API int hts_autotune(hts_ctx *ctx, double theta, int reps, int *tuning);
  * about 2048 warps, within a partial-sum buffer of
  * min(64 n, 2^22) entries for n <= 262144 (no split above).  Errors: HTS_EINVAL (depth < -1 or > 3). */
 HTS_API int hts_set_walk_split(hts_ctx *ctx, int depth);
+/* The cut depth in use (the automatic choice resolved; 0 with segments).
+ * hts_autotune also times every depth the buffer allows on the current
+ * problem and keeps the fastest.  Errors: HTS_EINVAL. */
+HTS_API int hts_get_walk_split(const hts_ctx *ctx, int *depth);
 HTS_API int hts_set_tuning(hts_ctx *ctx, int walk_block, int attract_lanes);
 HTS_API int hts_get_tuning(const hts_ctx *ctx, int *tuning);
 

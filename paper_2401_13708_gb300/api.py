@@ -209,6 +209,12 @@ class HyperbolicTSNE:
         """Cut depth (0..3) of the split walk for small problems; -1 chooses by size."""
         self._check(self._lib.hts_set_walk_split(self._ctx, int(depth)))
 
+    def get_walk_split(self) -> int:
+        """The split walk's cut depth in use (the automatic choice resolved)."""
+        d = C.c_int(0)
+        self._check(self._lib.hts_get_walk_split(self._ctx, C.byref(d)))
+        return int(d.value)
+
     def get_tuning(self):
         out = (C.c_int * 2)()
         self._check(self._lib.hts_get_tuning(self._ctx, out))

@@ -184,6 +184,7 @@ int status_error(hts_ctx *c, int st)
 
 constexpr int kPhases = 6;  // keys, sort, tree, walk/exact, attract, Z + update
 constexpr int kEvents = kPhases + 3;  // per iteration: 6 marks on the main stream, 2 on the side stream
+constexpr int kMaxSplitCut = 3;      // deepest cut the autotuner tries (hts_set_walk_split's range)
 constexpr int kAttractAfter = 3;      // stage after which the attraction forks: 0 prep, 1 keys, 2 sort, 3 tree
 
 // Repulsion, attraction and Z for the current Y (results in frep, zi, fattr,
@@ -1146,6 +1147,22 @@ int hts_autotune(hts_ctx *c, double theta, int reps, int *tuning)
                 }
             }
             c->walk_block = pick;
+            // warps per chunk: the cut depth of the split walk (small problems)
+            const int dmax = walk_split_depth(c->n, kMaxSplitCut, c->cfg.precision == HTS_FP64);
+            if (c->nseg == 1 && dmax > 0) {
+                float bestd = INFINITY;
+                int pickd = 0;
+                for (int d = 0; d <= dmax; ++d) {
+                    c->walk_split = d;
+                    float ms = 0.f;
+                    if ((r = time_it([&] { launch_walk(c); }, &ms))) return r;
+                    if (ms < bestd) {
+                        bestd = ms;
+                        pickd = d;
+                    }
+                }
+                c->walk_split = pickd;
+            }
         }
         if (c->nnz > 0 && c->cfg.precision == HTS_FP32_MIXED) {
             const int cand[4] = {4, 8, 16, 32};
@@ -1194,6 +1211,13 @@ int hts_set_walk_split(hts_ctx *c, int depth)
     if (depth < -1 || depth > 3) return fail(c, HTS_EINVAL, "hts_set_walk_split: depth in -1 .. 3");
     c->walk_split = depth;
     c->layout_version += 1;
+    return HTS_OK;
+}
+
+int hts_get_walk_split(const hts_ctx *c, int *depth)
+{
+    if (!c || !depth) return HTS_EINVAL;
+    *depth = c->nseg > 1 ? 0 : walk_split_depth(c->n, c->walk_split, c->cfg.precision == HTS_FP64);
     return HTS_OK;
 }
 

@@ -59,9 +59,11 @@ def test_autotune_then_parity():
     w, y = problem()
     ref = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=0.5, exag=1.0)
     with ctx("fp32") as t:
+        assert t.get_walk_split() == 3          # 3001 points: 94 chunks, the deepest cut by default
         wb, lanes = t.autotune(0.5, 3)
         assert wb in (32, 64, 128, 256) and lanes in (4, 8, 16, 32)
         assert t.get_tuning() == (wb, lanes)
+        assert 0 <= t.get_walk_split() <= 3     # timed at every depth
         g, Z = t.grad(0.5, 1.0)
         assert rel(g, ref["g"]) < 1e-3
         assert Z == pytest.approx(ref["Z"], rel=1e-4)
