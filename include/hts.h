@@ -114,9 +114,10 @@ HTS_API void hts_destroy(hts_ctx *ctx);
  * dtype HTS_F32 | HTS_F64; in HTS_FP32_MIXED the values are kept as float32,
  * in HTS_FP64 as float64.  Host inputs are validated (monotone indptr,
  * indices in range and off-diagonal, finite non-negative values); device
- * inputs are validated on the device.  Errors: HTS_EINVAL, HTS_ESHAPE (bad
- * CSR or n differs from a Y already set), HTS_EDOMAIN (bad values),
- * HTS_EOOM, HTS_ECUDA. */
+ * inputs are validated on the device.  After an error past the argument
+ * checks the context holds no P until the next successful call.  Errors:
+ * HTS_EINVAL, HTS_ESHAPE (bad CSR or n differs from a Y already set),
+ * HTS_EDOMAIN (bad values), HTS_EOOM, HTS_ECUDA. */
 HTS_API int hts_set_P(hts_ctx *ctx, int64_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
               const void *values, int dtype, int where);
 

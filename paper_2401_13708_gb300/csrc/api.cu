@@ -555,6 +555,8 @@ int hts_set_P(hts_ctx *c, int64_t n, int64_t nnz, const int64_t *indptr, const i
         if ((r = check_device_ptr(c, indptr))) return r;
         if (nnz > 0 && ((r = check_device_ptr(c, indices)) || (r = check_device_ptr(c, values)))) return r;
     }
+    c->have_P = false;  // the buffers change below: no P until this call succeeds
+    c->layout_version += 1;
     if ((r = dalloc(c, &c->indptr, (size_t)n + 1))) return r;
     if ((r = dalloc(c, &c->indices, (size_t)nnz))) return r;
     if (out_f64) {
@@ -857,7 +859,16 @@ int hts_get_tree(hts_ctx *c, int64_t cap, int64_t *count_out, int32_t *depth, ui
     }
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     const size_t M = 2 * (size_t)n;
-    TreeExport ex{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // export arrays, freed on every return path
+    struct Owned {
+        TreeExport ex{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        ~Owned()
+        {
+            cudaFree(ex.depth); cudaFree(ex.prefix); cudaFree(ex.count); cudaFree(ex.first);
+            cudaFree(ex.ycell); cudaFree(ex.rcell);
+        }
+    } own;
+    TreeExport &ex = own.ex;
     bool want = cap > 0;
     if (want) {
         CK(cudaMalloc((void **)&ex.depth, M * sizeof(int32_t)));
@@ -875,13 +886,7 @@ int hts_get_tree(hts_ctx *c, int64_t cap, int64_t *count_out, int32_t *depth, ui
     int m = 0;
     CK(cudaMemcpyAsync(&m, c->n_nodes, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (m < 0 || m > (int64_t)M) {
-        if (want) {
-            cudaFree(ex.depth); cudaFree(ex.prefix); cudaFree(ex.count); cudaFree(ex.first);
-            cudaFree(ex.ycell); cudaFree(ex.rcell);
-        }
-        return fail(c, HTS_ENUMERIC, "hts_get_tree: node count out of range");
-    }
+    if (m < 0 || m > (int64_t)M) return fail(c, HTS_ENUMERIC, "hts_get_tree: node count out of range");
     if (count_out) *count_out = m;
     int st = 0;
     if ((r = read_status(c, &st))) return r;
@@ -897,8 +902,6 @@ int hts_get_tree(hts_ctx *c, int64_t cap, int64_t *count_out, int32_t *depth, ui
             if (ycell) cudaMemcpy(ycell, ex.ycell, 2 * m * sizeof(double), cudaMemcpyDeviceToHost);
             if (rcell) cudaMemcpy(rcell, ex.rcell, m * sizeof(double), cudaMemcpyDeviceToHost);
         }
-        cudaFree(ex.depth); cudaFree(ex.prefix); cudaFree(ex.count); cudaFree(ex.first);
-        cudaFree(ex.ycell); cudaFree(ex.rcell);
         if (rc) return rc;
     }
     return status_error(c, st);
