@@ -95,6 +95,7 @@ int ensure_points(hts_ctx *c, int64_t n)
 {
     if (n == c->cap_n && (c->pts32 || c->pts64)) return HTS_OK;
     const size_t N = (size_t)std::max<int64_t>(n, 1);
+    c->cap_n = -1;  // until every buffer below has its new size
     int r;
 #define AL(ptr, cnt) \
     if ((r = dalloc(c, &(ptr), (cnt))) != HTS_OK) return r
@@ -644,6 +645,7 @@ int hts_set_Y(hts_ctx *c, int64_t n, const double *y, int where)
     if (n != c->n && c->nseg > 1) free_segments(c);
     // buffers move (and captured graphs go stale) only when the size changes
     if (n != c->n || n != c->cap_n || !(c->pts32 || c->pts64)) c->layout_version += 1;
+    c->have_Y = false;  // until this call succeeds
     if ((r = ensure_points(c, n))) return r;
     if (n > 0) {
         CK(cudaMemcpyAsync(c->y, y, sizeof(double2) * (size_t)n,
