@@ -279,6 +279,22 @@ def test_graph_replay_is_bit_identical(segmented):
     assert np.array_equal(out[0], out[1])
 
 
+def test_graph_replay_multi_tile_sort():
+    """A captured iteration whose key sort spans several 4096-key tiles (9000
+    points: one-sweep passes with look-back) replays bit-identically."""
+    w = inputs.make_workload("gaussian_mixture", seed=6, n=9000)
+    y = inputs.spread_embedding(w.labels, 6)
+    out = []
+    for graphs in (False, True):
+        with HyperbolicTSNE(precision="fp32") as t:
+            t.set_P(w.indptr, w.indices, w.values)
+            t.set_Y(y)
+            t.set_graphs(graphs)
+            t.step(6, 0.5, 12.0, w.n / 12000.0, 0.5)
+            out.append(t.get_Y())
+    assert np.array_equal(out[0], out[1])
+
+
 def test_cosne_term_per_segment():
     """With segments the CO-SNE term of each point uses its segment's size."""
     w, y = batch()

@@ -93,6 +93,22 @@ def test_tree_matches_oracle(name, rule):
     assert np.allclose(g["rcell"][fin], o["rcell"][fin], rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("n", [4096, 4097, 262145])
+def test_tree_across_sort_paths(n):
+    """The key sort runs in one block up to one 4096-key tile and as one-sweep
+    passes with decoupled look-back above; both sides of the boundary, and 65
+    tiles of look-back, build the oracle's tree."""
+    import torch
+    w = inputs.make_workload("single_cell", seed=n % 7, n=n,
+                             device="cuda" if torch.cuda.is_available() else "cpu")
+    y = inputs.spread_embedding(w.labels, n % 5, rho_hi=10.0)
+    with make("fp32", w, y) as t:
+        g = t.get_tree()
+    o = oracle.tree_export(y, 0, which=1)
+    for k in ("depth", "prefix", "count", "first"):
+        assert np.array_equal(g[k], o[k]), k
+
+
 @pytest.mark.parametrize("name", ["mixture", "mixture_init", "ragged"])
 def test_exact_fp64(name):
     w, y = workload(name)
