@@ -215,8 +215,10 @@ HTS_API int hts_set_profiling(hts_ctx *ctx, int enable);
 HTS_API int hts_get_profile(hts_ctx *ctx, double *ms6, int64_t *iters);
 
 /* Optimiser state for checkpoint/resume: velocity and gains (n x 2 float64
- * each) and the number of iterations run.  get: outputs may be NULL.
- * set: NULL leaves a part unchanged.  Errors: HTS_ENOTSET, HTS_ECUDA. */
+ * each, in `where` memory) and the number of iterations run.  get: outputs
+ * may be NULL.  set: NULL leaves a part unchanged; iters >= 0.  Errors:
+ * HTS_ENOTSET, HTS_EINVAL (bad `where`, negative iters, or a pointer given as
+ * HTS_DEVICE that is not device memory of the context's device), HTS_ECUDA. */
 HTS_API int hts_get_state(hts_ctx *ctx, double *vel, double *gains, int64_t *iters, int where);
 HTS_API int hts_set_state(hts_ctx *ctx, const double *vel, const double *gains, int64_t iters, int where);
 

@@ -482,7 +482,12 @@ void hts_destroy(hts_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->cfg.device);
+    // every stream of the context is idle before a buffer is freed (a failed
+    // call can leave work on a side stream that was never joined)
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    if (c->pstream) cudaStreamSynchronize(c->pstream);
+    if (c->astream) cudaStreamSynchronize(c->astream);
+    if (c->gstream) cudaStreamSynchronize(c->gstream);
     dfree(&c->indptr); dfree(&c->indices); dfree(&c->values);
     dfree(&c->y); dfree(&c->vel); dfree(&c->gains); dfree(&c->fattr); dfree(&c->frep);
     dfree(&c->zi); dfree(&c->radial); dfree(&c->pts32); dfree(&c->pts64);
@@ -497,20 +502,11 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->dscal); dfree(&c->status); dfree(&c->counters); dfree(&c->xsq);
     dfree(&c->seg_off); dfree(&c->seg_of); dfree(&c->seg_lr); dfree(&c->seg_z);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->gstream) {
-        cudaStreamSynchronize(c->gstream);
-        cudaStreamDestroy(c->gstream);
-    }
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->gev_in) cudaEventDestroy(c->gev_in);
     if (c->gev_out) cudaEventDestroy(c->gev_out);
-    if (c->astream) {
-        cudaStreamSynchronize(c->astream);
-        cudaStreamDestroy(c->astream);
-    }
-    if (c->pstream) {
-        cudaStreamSynchronize(c->pstream);
-        cudaStreamDestroy(c->pstream);
-    }
+    if (c->astream) cudaStreamDestroy(c->astream);
+    if (c->pstream) cudaStreamDestroy(c->pstream);
     if (c->aev_fork) cudaEventDestroy(c->aev_fork);
     if (c->aev_join) cudaEventDestroy(c->aev_join);
     if (c->pev_in) cudaEventDestroy(c->pev_in);
@@ -731,6 +727,10 @@ int hts_step(hts_ctx *c, int n_iter, double theta, double exaggeration, double l
             if (!r && ev && cudaEventRecord(ev[6], c->stream) != cudaSuccess) r = fail(c, HTS_ECUDA, "event");
         }
         c->stream = user;
+        if (r) {  // a failed iteration may have left the attraction unjoined
+            CK(cudaEventRecord(c->aev_join, c->astream));
+            CK(cudaStreamWaitEvent(c->pstream, c->aev_join, 0));
+        }
         CK(cudaEventRecord(c->pev_out, c->pstream));
         CK(cudaStreamWaitEvent(c->stream, c->pev_out, 0));
         if (r) return r;
@@ -897,12 +897,12 @@ int hts_get_tree(hts_ctx *c, int64_t cap, int64_t *count_out, int32_t *depth, ui
         if (cap < m) {
             rc = fail(c, HTS_EINVAL, "hts_get_tree: cap smaller than the node count");
         } else {
-            if (depth) cudaMemcpy(depth, ex.depth, m * sizeof(int32_t), cudaMemcpyDeviceToHost);
-            if (prefix) cudaMemcpy(prefix, ex.prefix, m * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-            if (count) cudaMemcpy(count, ex.count, m * sizeof(int64_t), cudaMemcpyDeviceToHost);
-            if (first) cudaMemcpy(first, ex.first, m * sizeof(int64_t), cudaMemcpyDeviceToHost);
-            if (ycell) cudaMemcpy(ycell, ex.ycell, 2 * m * sizeof(double), cudaMemcpyDeviceToHost);
-            if (rcell) cudaMemcpy(rcell, ex.rcell, m * sizeof(double), cudaMemcpyDeviceToHost);
+            if (depth) CK(cudaMemcpy(depth, ex.depth, m * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            if (prefix) CK(cudaMemcpy(prefix, ex.prefix, m * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+            if (count) CK(cudaMemcpy(count, ex.count, m * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            if (first) CK(cudaMemcpy(first, ex.first, m * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            if (ycell) CK(cudaMemcpy(ycell, ex.ycell, 2 * m * sizeof(double), cudaMemcpyDeviceToHost));
+            if (rcell) CK(cudaMemcpy(rcell, ex.rcell, m * sizeof(double), cudaMemcpyDeviceToHost));
         }
         if (rc) return rc;
     }
@@ -957,8 +957,12 @@ int hts_get_state(hts_ctx *c, double *vel, double *gains, int64_t *iters, int wh
 {
     if (!c) return HTS_EINVAL;
     if (!c->have_Y) return fail(c, HTS_ENOTSET, "Y is not set");
+    if (where != HTS_HOST && where != HTS_DEVICE) return fail(c, HTS_EINVAL, "hts_get_state: bad where");
     int r = set_device(c);
     if (r) return r;
+    if (where == HTS_DEVICE && c->n &&
+        ((vel && (r = check_device_ptr(c, vel))) || (gains && (r = check_device_ptr(c, gains)))))
+        return r;
     cudaMemcpyKind k = where == HTS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (vel && c->n) CK(cudaMemcpyAsync(vel, c->vel, sizeof(double2) * (size_t)c->n, k, c->stream));
     if (gains && c->n) CK(cudaMemcpyAsync(gains, c->gains, sizeof(double2) * (size_t)c->n, k, c->stream));
@@ -971,8 +975,13 @@ int hts_set_state(hts_ctx *c, const double *vel, const double *gains, int64_t it
 {
     if (!c) return HTS_EINVAL;
     if (!c->have_Y) return fail(c, HTS_ENOTSET, "Y is not set");
+    if (where != HTS_HOST && where != HTS_DEVICE) return fail(c, HTS_EINVAL, "hts_set_state: bad where");
+    if (iters < 0) return fail(c, HTS_EINVAL, "hts_set_state: negative iteration count");
     int r = set_device(c);
     if (r) return r;
+    if (where == HTS_DEVICE && c->n &&
+        ((vel && (r = check_device_ptr(c, vel))) || (gains && (r = check_device_ptr(c, gains)))))
+        return r;
     cudaMemcpyKind k = where == HTS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (vel && c->n) CK(cudaMemcpyAsync(c->vel, vel, sizeof(double2) * (size_t)c->n, k, c->stream));
     if (gains && c->n) CK(cudaMemcpyAsync(c->gains, gains, sizeof(double2) * (size_t)c->n, k, c->stream));

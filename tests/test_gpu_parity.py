@@ -310,6 +310,16 @@ def test_input_validation():
            torch.tensor([0.5, 0.5], dtype=torch.float64, device="cuda"))
     with pytest.raises(HtsError, match="ESHAPE"):
         t.set_P(*dev)
+    # optimiser state: a bad memory kind, a negative count, a host pointer given as device memory
+    import ctypes as C
+    t.set_P(*ok)
+    v = np.zeros((2, 2))
+    vp = v.ctypes.data_as(C.c_void_p)
+    assert t._lib.hts_set_state(t._ctx, vp, None, 0, 7) == -1          # HTS_EINVAL
+    assert t._lib.hts_set_state(t._ctx, vp, None, -1, 0) == -1
+    assert t._lib.hts_get_state(t._ctx, vp, None, None, 1) == -1       # host array as HTS_DEVICE
+    t.set_state(np.full((2, 2), 1e-3), None, 5)
+    assert t.get_state()[2] == 5
     t.close()
 
 
