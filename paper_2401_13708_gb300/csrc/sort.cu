@@ -6,7 +6,8 @@
 //   digit_hist  once per sort: the global histograms of all eight digits
 //               (they do not depend on the order of the keys), then an
 //               exclusive scan of each gives every digit its first slot;
-//   onesweep    per pass, one 4096-key tile per block, tiles taken in launch
+//   onesweep    per pass, one tile per block (1024, 2048 or 4096 keys by
+//               problem size, tile_keys), tiles taken in launch
 //               order from an atomic counter: warp histograms (match_any +
 //               popc), the tile's per-digit counts published to a status
 //               word, and a decoupled look-back over earlier tiles (thread d
@@ -26,11 +27,10 @@
 namespace hts {
 namespace {
 
-constexpr int kTile = 4096;
+constexpr int kSmallMax = 4096;    // up to this many keys, one block sorts (small_sort_kernel)
+constexpr int kMinTile = 1024;     // one-sweep tiles hold 1024, 2048 or 4096 keys (tile_keys)
 constexpr int kSortThreads = 256;
 constexpr int kWarps = kSortThreads / 32;
-constexpr int kPerWarp = kTile / kWarps;   // 512
-constexpr int kRounds = kPerWarp / 32;     // 16
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
@@ -41,7 +41,19 @@ constexpr unsigned long long kFlagPre = 2ull << 62;   // inclusive prefix publis
 constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
 constexpr int kSpinLimit = 1 << 22;
 
+// Keys per one-sweep tile.  A pass is latency-bound: one block ranks and
+// writes its tile in kTile / 256 sequential rounds, so smaller tiles finish
+// sooner while there are SMs to spare; large problems keep 4096-key tiles
+// (fewer look-back steps and status words).  Measured sort times per
+// iteration: 20,000 keys 156 / 110 / 87 us with 4096 / 2048 / 1024-key tiles,
+// 262,145 keys 174 / 143 / 152 us, 1,000,000 keys 283 / 295 / 301 us.
+int tile_keys(int64_t n)
+{
+    return n <= 196608 ? 1024 : n <= 524288 ? 2048 : 4096;
+}
+
 // Global histograms of all eight digits; hist[pass][digit] (2048 ints).
+template <int kTile>
 __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint64_t *__restrict__ keys, int n,
                                                                   int *hist)
 {
@@ -94,6 +106,7 @@ __global__ void digit_offsets_kernel(int *hist)
     }
 }
 
+template <int kTile>
 __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *__restrict__ kin,
                                                                 const uint32_t *__restrict__ vin,
                                                                 uint64_t *__restrict__ kout,
@@ -102,6 +115,8 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
                                                                 unsigned long long *tile_status, int *tile_ctr,
                                                                 int *status)
 {
+    constexpr int kPerWarp = kTile / kWarps;
+    constexpr int kRounds = kPerWarp / 32;
     __shared__ int wh[kWarps][256];
     __shared__ int s_tile;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -268,7 +283,7 @@ int scan_exclusive(const int *in, int *out, int64_t len, int *tmp, cudaStream_t 
 
 namespace {
 
-// n <= kTile: all eight passes in one block (no look-back: the block's own
+// n <= kSmallMax: all eight passes in one block (no look-back: the block's own
 // histogram is the global one), ping-ponging through the two key buffers.
 // ROUNDS keys per lane: 256 * ROUNDS >= n (fewer rounds for fewer keys).
 template <int ROUNDS>
@@ -355,22 +370,23 @@ __global__ void __launch_bounds__(kSortThreads) small_sort_kernel(uint64_t *ka, 
 
 size_t sort_status_words(int64_t n)
 {
-    const int64_t tiles = (n + kTile - 1) / kTile;
+    const int64_t tiles = (n + kMinTile - 1) / kMinTile;  // the most tiles any size up to n uses
     return (size_t)kPasses * 256 * (size_t)std::max<int64_t>(tiles, 1);
 }
 
 void launch_sort_pairs(hts_ctx *c)
 {
     const int n = (int)c->n;
-    const int tiles = (n + kTile - 1) / kTile;
-    if (tiles == 1) {  // one block does all eight passes
+    const int tile = tile_keys(n);
+    const int tiles = (n + tile - 1) / tile;
+    static_assert(kSmallMax == kSortThreads * 16, "small_sort_kernel<16> covers kSmallMax keys");
+    if (n <= kSmallMax) {  // one block does all eight passes
         if (n <= kSortThreads * 4)
             small_sort_kernel<4><<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt, n);
         else if (n <= kSortThreads * 8)
             small_sort_kernel<8><<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt, n);
         else
-            small_sort_kernel<kRounds><<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt,
-                                                                          n);
+            small_sort_kernel<16><<<1, kSortThreads, 0, c->stream>>>(c->keys, c->idx, c->keys_alt, c->idx_alt, n);
         c->launches += 1;
         return;
     }
@@ -380,14 +396,27 @@ void launch_sort_pairs(hts_ctx *c)
     unsigned long long *stat = reinterpret_cast<unsigned long long *>(c->sort_scratch + (kPasses * 256 + 64) / 2);
     cudaMemsetAsync(c->sort_scratch, 0, sizeof(unsigned long long) * ((kPasses * 256 + 64) / 2 +
                                                                       (size_t)kPasses * 256 * tiles), c->stream);
-    digit_hist_kernel<<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
+    if (tile == 1024)
+        digit_hist_kernel<1024><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
+    else if (tile == 2048)
+        digit_hist_kernel<2048><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
+    else
+        digit_hist_kernel<4096><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
     digit_offsets_kernel<<<1, 32 * kPasses, 0, c->stream>>>(hist);
     c->launches += 2 + kPasses;
     uint64_t *ka = c->keys, *kb = c->keys_alt;
     uint32_t *va = c->idx, *vb = c->idx_alt;
     for (int p = 0; p < kPasses; ++p) {
-        onesweep_kernel<<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
-                                                               stat + (size_t)p * 256 * tiles, ctr + p, c->status);
+        unsigned long long *sp = stat + (size_t)p * 256 * tiles;
+        if (tile == 1024)
+            onesweep_kernel<1024><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
+                                                                         sp, ctr + p, c->status);
+        else if (tile == 2048)
+            onesweep_kernel<2048><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
+                                                                         sp, ctr + p, c->status);
+        else
+            onesweep_kernel<4096><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
+                                                                         sp, ctr + p, c->status);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }

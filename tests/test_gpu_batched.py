@@ -280,8 +280,8 @@ def test_graph_replay_is_bit_identical(segmented):
 
 
 def test_graph_replay_multi_tile_sort():
-    """A captured iteration whose key sort spans several 4096-key tiles (9000
-    points: one-sweep passes with look-back) replays bit-identically."""
+    """A captured iteration whose key sort spans several one-sweep tiles (9000
+    points: nine 1024-key tiles with look-back) replays bit-identically."""
     w = inputs.make_workload("gaussian_mixture", seed=6, n=9000)
     y = inputs.spread_embedding(w.labels, 6)
     out = []

@@ -93,16 +93,17 @@ def test_tree_matches_oracle(name, rule):
     assert np.allclose(g["rcell"][fin], o["rcell"][fin], rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("n", [4096, 4097, 262145])
+@pytest.mark.parametrize("n", [4096, 4097, 196608, 196609, 524288, 524289])
 def test_tree_across_sort_paths(n):
-    """The key sort runs in one block up to one 4096-key tile and as one-sweep
-    passes with decoupled look-back above; both sides of the boundary, and 65
-    tiles of look-back, build the oracle's tree."""
-    import torch
-    w = inputs.make_workload("single_cell", seed=n % 7, n=n,
-                             device="cuda" if torch.cuda.is_available() else "cpu")
-    y = inputs.spread_embedding(w.labels, n % 5, rho_hi=10.0)
-    with make("fp32", w, y) as t:
+    """The key sort runs in one block up to 4096 keys and as one-sweep passes
+    with decoupled look-back above, in tiles of 1024 keys up to 196,608 keys,
+    2048 up to 524,288 and 4096 beyond; both sides of every boundary build the
+    oracle's tree.  (P plays no part in the tree: it is empty here.)"""
+    labels = (np.arange(n) * 7919) % 37
+    y = inputs.spread_embedding(labels, n % 5, rho_hi=10.0)
+    with HyperbolicTSNE(precision="fp32") as t:
+        t.set_P(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+        t.set_Y(y)
         g = t.get_tree()
     o = oracle.tree_export(y, 0, which=1)
     for k in ("depth", "prefix", "count", "first"):
