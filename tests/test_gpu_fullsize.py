@@ -6,7 +6,8 @@ batch), the context is set up as the benchmark sets it up (launch shapes
 from the autotuner), and the gradient is compared with the FP64 oracle on
 sampled rows: the oracle builds its own tree over all points, walks every
 point for Z, and evaluates the sampled rows one by one.  Bars as in the
-small-size tests: FP64 relative 1e-9, FP32-mixed relative L2 1e-3 (Z 1e-4).
+small-size tests: FP64 relative 1e-9, FP32-mixed relative L2 1e-3 (Z 1e-4)
+and the per-row bar of bars.py.
 The states are Y0 ~ N(0, 1e-4 I) (the protocol's start) and a synthetic
 rim-heavy spread state; neither comes from the CUDA path.
 """
@@ -14,12 +15,11 @@ import numpy as np
 import pytest
 
 import oracle
+from bars import FP32_ROW_TOL, FP32_TOL, FP64_TOL, rel, worst_row
 from paper_2401_13708_gb300 import HyperbolicTSNE, inputs
 
 pytestmark = pytest.mark.gpu
 
-FP64_TOL = 1e-9
-FP32_TOL = 1e-3
 ROWS = 2000
 
 _cache = {}
@@ -32,10 +32,6 @@ def workload(name):
         w = inputs.make_workload(name, seed=0, device=dev)
         _cache[name] = (w, inputs.spread_embedding(w.labels, 0))
     return _cache[name]
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 def rows_for(n, seed=7):
@@ -65,6 +61,7 @@ def test_fullsize_fp32_sampled_rows(name, theta, state):
     g, Z = gpu_grad("fp32", w, y, theta)
     assert Z == pytest.approx(ref["Z"], rel=1e-4)
     assert rel(g[rows], ref["g"]) < FP32_TOL
+    assert worst_row(g[rows], ref) < FP32_ROW_TOL
 
 
 @pytest.mark.parametrize("name,theta", [("binary_tree", 0.2), ("binary_tree", 0.8), ("single_cell", 0.5)])
@@ -103,3 +100,4 @@ def test_fullsize_batched_segments():
         ref = oracle.bh_grad(y[a:b], ip, ix, w.values[e0:e1], theta=0.5, exag=1.0)
         assert zs[s] == pytest.approx(ref["Z"], rel=1e-4)
         assert rel(g[a:b], ref["g"]) < FP32_TOL
+        assert worst_row(g[a:b], ref) < FP32_ROW_TOL

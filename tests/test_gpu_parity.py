@@ -6,7 +6,8 @@ Bars (from the arithmetic each path uses):
     sums through the same float64 formula);
   * HTS_FP64 gradient, Z, KL and 10 steps of positions: relative 1e-9;
   * HTS_FP32_MIXED gradient: relative L2 error <= 1e-3 against the oracle at
-    the same theta (the paper's own BH-vs-exact error is 1e-3 .. 2.7e-3).
+    the same theta (the paper's own BH-vs-exact error is 1e-3 .. 2.7e-3), and
+    every row within 1e-3 of the size of its two force terms (bars.py).
 Sizes span several 32-point warps, 256-thread blocks and 4096-key sort
 tiles, with ragged tails.
 """
@@ -16,20 +17,10 @@ import numpy as np
 import pytest
 
 import oracle
+from bars import FP32_ROW_TOL, FP32_TOL, FP64_TOL, maxrel, rel, worst_row
 from paper_2401_13708_gb300 import HyperbolicTSNE, inputs
 
 pytestmark = pytest.mark.gpu
-
-FP64_TOL = 1e-9
-FP32_TOL = 1e-3
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
-
-
-def maxrel(a, b):
-    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
 
 
 def make(precision, w, y, **kw):
@@ -142,6 +133,7 @@ def test_bh_fp32_mixed(name, theta):
         g, Z = t.grad(theta, 1.0)
     assert Z == pytest.approx(ref["Z"], rel=1e-4)
     assert rel(g, ref["g"]) < FP32_TOL
+    assert worst_row(g, ref) < FP32_ROW_TOL
 
 
 @pytest.mark.parametrize("name", ["mixture", "ragged"])
@@ -152,6 +144,7 @@ def test_exact_fp32_mixed(name):
         g, Z = t.grad(0.0, 12.0)
     assert Z == pytest.approx(ref["Z"], rel=1e-5)
     assert rel(g, ref["g"]) < FP32_TOL
+    assert worst_row(g, ref, 12.0) < FP32_ROW_TOL
 
 
 @pytest.mark.parametrize("theta", [0.0, 0.5])
@@ -189,6 +182,55 @@ def test_kl(theta):
         assert t.kl(theta) == pytest.approx(ref, rel=1e-10)
     with make("fp32", w, y) as t:
         assert t.kl(theta) == pytest.approx(ref, rel=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# Equal-area radial splits (Eq. EqualAreaSplitting): gradient, Z and steps
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["mixture", "ragged", "tree_small"])
+@pytest.mark.parametrize("theta", [0.2, 0.5, 0.8])
+def test_bh_fp64_equal_area(name, theta):
+    w, y = workload(name)
+    ref = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=theta, exag=1.0, split_rule=1)
+    with make("fp64", w, y, split_rule="equal_area") as t:
+        g, Z = t.grad(theta, 1.0)
+    assert Z == pytest.approx(ref["Z"], rel=1e-12)
+    assert rel(g, ref["g"]) < FP64_TOL
+    assert maxrel(g, ref["g"]) < FP64_TOL
+
+
+@pytest.mark.parametrize("name", ["mixture", "mixture_init", "ragged", "tree_small", "mnist_small"])
+@pytest.mark.parametrize("theta", [0.5, 0.8])
+def test_bh_fp32_mixed_equal_area(name, theta):
+    w, y = workload(name)
+    ref = oracle.bh_grad(y, w.indptr, w.indices, w.values, theta=theta, exag=1.0, split_rule=1)
+    with make("fp32", w, y, split_rule="equal_area") as t:
+        g, Z = t.grad(theta, 1.0)
+    assert Z == pytest.approx(ref["Z"], rel=1e-4)
+    assert rel(g, ref["g"]) < FP32_TOL
+    assert worst_row(g, ref) < FP32_ROW_TOL
+
+
+def test_steps_fp64_equal_area_track_oracle():
+    w, y = workload("mixture")
+    lr = w.n / 12000.0
+    yo, vo, _ = oracle.step(y, np.zeros_like(y), w.indptr, w.indices, w.values, 10, 0.5, 12.0, lr, 0.5,
+                            split_rule=1)
+    with make("fp64", w, y, split_rule="equal_area") as t:
+        t.step(10, 0.5, 12.0, lr, 0.5)
+        yg = t.get_Y()
+        vg, _, it = t.get_state()
+    assert it == 10
+    assert rel(yg, yo) < FP64_TOL
+    assert rel(vg, vo) < 1e-8
+
+
+def test_kl_equal_area():
+    w, y = workload("mixture")
+    ref = oracle.kl(y, w.indptr, w.indices, w.values, theta=0.5, split_rule=1)
+    with make("fp64", w, y, split_rule="equal_area") as t:
+        assert t.kl(0.5) == pytest.approx(ref, rel=1e-10)
 
 
 def test_paper_printed_gradient_form():
