@@ -4,18 +4,21 @@
 // theta = 0 in HTS_FP64 (exact repulsion over all pairs, attraction over P,
 // Z, g = 4 (exag F_attr - F_rep / Z)), but keeps its work arrays in one
 // file-scope __device__ array of fixed size instead of buffers from
-// cudaMalloc.  It exists for callers that must not allocate device memory:
-// code that issues work while a CUDA graph is being captured (cudaMalloc is
-// not allowed there), and plug-ins living inside a framework or server whose
-// allocator owns the whole memory budget.  Such callers pass device pointers
-// for every input and output.
+// cudaMalloc.  It exists for callers that cannot allocate device memory
+// themselves or through this library: a plug-in inside a framework or an
+// inference server whose own allocator owns the whole device memory budget
+// (a cudaMalloc behind its back can fail or starve it), and code on a
+// latency-critical path where the implicit device synchronisation of
+// cudaMalloc / cudaFree is not acceptable.  Such callers pass device
+// pointers for every input and output.
 //
 // The array holds HTS_NOALLOC_MAX_N points (about 4.5 MB) and stays resident
 // on every device that loads this library, until the process exits.  All
-// calls share it: a call writes every element it later reads, so nothing has
-// to be cleared between calls, but two calls whose kernels overlap on the
-// GPU (different streams, or different host threads on one device) race on
-// it and must be serialised by the caller.
+// calls share it: a call writes every element it later reads (the one flag
+// that must start at zero is cleared at the start of each call), but two
+// calls whose kernels overlap on the GPU (different streams, or different
+// host threads on one device) race on it and must be serialised by the
+// caller.
 #include <mutex>
 
 #include "hts_internal.cuh"
@@ -37,6 +40,7 @@ struct Scratch {
     double zi[kMaxN];        // per-point Z terms
     double partial[kRedBlocks];
     double Z;
+    int bad;                 // set when a point is outside the open disk or not finite
 };
 
 static __device__ __align__(256) Scratch g_scratch;
@@ -63,12 +67,19 @@ int scratch_address(int device, Scratch **out)
     return HTS_OK;
 }
 
+// Point records; a point with |y| >= 1 or a non-finite coordinate sets
+// s->bad, which turns g and Z into NaN (na_final_z, na_combine).
 __global__ void na_prep(int n, const double2 *__restrict__ y, Scratch *s)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= n) return;
     double2 p = y[i];
     double n2 = p.x * p.x + p.y * p.y;
+    if (!isfinite(p.x) || !isfinite(p.y) || !(n2 < 1.0)) {
+        atomicOr(&s->bad, 1);
+        p = make_double2(0.0, 0.0);  // keeps the later kernels' arithmetic finite
+        n2 = 0.0;
+    }
     s->pts[i] = PointD{p.x, p.y, 1.0 / (1.0 - n2), 0.0};
 }
 
@@ -166,8 +177,9 @@ __global__ void __launch_bounds__(kRedBlocks) na_final_z(Scratch *s, double *Z_o
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        s->Z = sh[0];
-        if (Z_out) *Z_out = sh[0];
+        const double Z = s->bad ? __longlong_as_double(0x7FF8000000000000ll) : sh[0];  // NaN: a point out of range
+        s->Z = Z;
+        if (Z_out) *Z_out = Z;
     }
 }
 
@@ -175,6 +187,11 @@ __global__ void na_combine(int n, double exag, const Scratch *s, double2 *g)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= n) return;
+    if (s->bad) {  // a point outside the open disk: no gradient
+        const double nan = __longlong_as_double(0x7FF8000000000000ll);
+        g[i] = make_double2(nan, nan);
+        return;
+    }
     const double invZ = s->Z > 0.0 ? 1.0 / s->Z : 0.0;
     const double2 fa = s->fattr[i], fr = s->frep[i];
     g[i] = make_double2(4.0 * (exag * fa.x - fr.x * invZ), 4.0 * (exag * fa.y - fr.y * invZ));
@@ -202,6 +219,10 @@ extern "C" int hts_exact_grad_noalloc(int64_t n, int64_t nnz, const double *y, c
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = (int)((n + kBlock - 1) / kBlock);
     const int rb = (int)((n * 32 + kBlock - 1) / kBlock);
+    if (cudaMemsetAsync(&s->bad, 0, sizeof(int), st) != cudaSuccess) {  // not an allocation
+        cudaGetLastError();
+        return HTS_ECUDA;
+    }
     na_prep<<<nb, kBlock, 0, st>>>((int)n, (const double2 *)y, s);
     if (grad_form == HTS_EXACT_KL) {
         na_repulsion<0><<<nb, kBlock, 0, st>>>((int)n, s);
