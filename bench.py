@@ -218,11 +218,14 @@ def run_reference(args, rank, world):
     t_s = float(np.mean(times))
     t_full = t_tree + (n / rows_per_step) * t_s
     value = 1.0 / t_full
-    sample = (f"oracle tree (literal insertion) built once over all {n} points ({t_tree:.2f} s); each step "
-              f"walks {rows_per_step} random rows (BH repulsion + attraction, {t_s * 1e3:.1f} ms); "
-              f"iteration time = t_tree + (N / rows) t_step")
+    sample = (f"oracle tree (literal insertion) built once over all {n} points ({t_tree:.2f} s); each timed "
+              f"step walks {rows_per_step} random rows (BH repulsion + attraction, {t_s * 1e3:.1f} ms); "
+              f"value = 1 / (t_tree + (N / rows) t_step), a full iteration extrapolated from the samples")
+    # ms_per_step is the time of one timed (sampled) step, as run; the rate of
+    # a full iteration is extrapolated from it (ms_per_iteration)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_s * 1e3,
+            "ms_per_iteration": t_full * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(n, args.theta),
                        "n": n, "nnz": w.nnz, "theta": args.theta},
@@ -243,16 +246,18 @@ def _cuda():
 # our arm
 # ---------------------------------------------------------------------------
 
-# Algorithmic FP32 operations of the tree walk (counted from the source
-# expressions of walk_f32_kernel / pair_terms_f32, an FMA counting 2):
-#   criterion per active lane at an internal cell: hi/lo difference (6),
-#     |Delta|^2 (3), delta (2), compare (1)                       -> 12
-#   pair term per interaction: clamp (1), delta (delta + 2) (2), sqrt (1),
-#     log1p (1), 1 + d^2 (2), rcp (1), w (1), rep (2), coefficient (2),
-#     accumulation (4 FMA = 8)                                    -> 21
-# A leaf interaction also forms Delta, s and delta (12).
-FLOPS_CRITERION = 12
-FLOPS_PAIR = 21
+# Algorithmic FP32 operations of the tree walk (counted from the expressions
+# of walk_f32_kernel / pair_terms_f32, an FMA counting 2):
+#   criterion test (an open lane at an internal cell): Delta (2), |Delta|^2
+#     (3), times 2 il_i (1), compare (1)                             -> 7
+#   interaction (accepted cell or leaf pair): Delta, |Delta|^2 and
+#     delta = 2 |Delta|^2 il_i il_c (7) + the pair term: clamp (1),
+#     delta (delta + 2) (2), sqrt (1), log1p (1), 1 + d^2 (2), rcp (1), w (1),
+#     rep (2), coefficient (2), accumulation (4 FMA = 8) (21)       -> 28
+# Criterion tests are counted on the device (hts_get_criterion_count), open
+# lanes only.
+FLOPS_CRITERION = 7
+FLOPS_INTERACTION = 28
 
 # Algorithmic DRAM bytes of the memory-bound phases (per point unless noted):
 #   keys    Y 16 read + point record 32 + radial 8 written, radial 8 read +
@@ -261,12 +266,13 @@ FLOPS_PAIR = 21
 #           (12 read + 12 written)                                      -> 200
 #   tree    gather 108 (index, Y, record in; sorted record, terms out),
 #           radix tree 52, fixed-point scan 168, marks/counts/scan 20,
-#           emit 144 (prefix sums in, 32-byte node out)                  -> ~490
-#   attract 8 per non-zero (index + value) + 24 per row (indptr, force)
-#           (the 32-byte neighbour records are gathered from L2)
+#           emit 144 (prefix sums in, two 16-byte node records out)       -> ~490
+#   attract per non-zero: index 4 + value 4 + the neighbour's position 8
+#           (16, counted although the gather is mostly served by L2); per
+#           row: indptr 8 + y_i 8 + force 8 (24)
 #   update  Y, velocity, both forces 64 read + Z 8 + Y, velocity 32 written -> 104
 BYTES_PER_POINT = {"keys": 76, "sort": 200, "tree": 490, "update": 104}
-ATTRACT_BYTES_PER_NNZ, ATTRACT_BYTES_PER_ROW = 8, 24
+ATTRACT_BYTES_PER_NNZ, ATTRACT_BYTES_PER_ROW = 16, 24
 
 
 def cpu_model():
@@ -285,6 +291,15 @@ def cpu_model():
     except Exception:
         pass
     return "unknown"
+
+
+def worst_row_err(g, ref, exag=1.0):
+    """max over rows of |g^_i - g_i| / (4 (exag |F_attr,i| + |F_rep,i| / Z)): each
+    row's error against the size of the two force terms whose difference is g_i."""
+    d = np.linalg.norm(np.asarray(g) - ref["g"], axis=1)
+    scale = 4.0 * (exag * np.linalg.norm(ref["fattr"], axis=1) + np.linalg.norm(ref["frep"], axis=1) / ref["Z"])
+    scale = np.maximum(np.maximum(scale, np.linalg.norm(ref["g"], axis=1)), 1e-300)
+    return float(np.max(d / scale)) if d.size else 0.0
 
 
 EARLY_ITERS = 250  # Sec. 5.2.1: 250 early-exaggeration iterations, then at most 750 plain ones
@@ -383,18 +398,17 @@ def run_ours(args, rank, world, local):
     t.set_counters(True)
     protocol(t, W, K, theta, lr)
     cnt = t.get_counters()
+    crit = t.criterion_count()
     t.set_counters(False)
     acc, pairs, visits, queries = [int(v) for v in cnt[:4]]
     replay_same = bool(np.array_equal(t.get_Y(), y_end))
 
     # ---- roofline of the dominant kernel (tree walk) --------------------
     walk_ms = prof["walk"] / max(piters, 1)
-    lane_visits = visits * 32  # criterion evaluations bounded by every lane of each warp visit
-    flops = (acc * FLOPS_PAIR + pairs * (FLOPS_PAIR + FLOPS_CRITERION) + lane_visits * FLOPS_CRITERION) / K
+    flops = ((acc + pairs) * FLOPS_INTERACTION + crit * FLOPS_CRITERION) / K
     sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1462.0
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     achieved = flops / (walk_ms * 1e-3) / 1e12
-    dominant = max(prof, key=prof.get)
     traffic = None  # DRAM bytes per walk launch from the committed ncu capture, scaled to n
     tf = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     if os.path.exists(tf):
@@ -417,6 +431,7 @@ def run_ours(args, rank, world, local):
     sprof, siters = t.get_profile()
     t.set_profiling(False)
     sphase = {k: v / max(siters, 1) for k, v in sprof.items()}
+    dominant = max(sphase, key=sphase.get)  # from the serial replay: each phase timed alone
     from paper_2401_13708_gb300 import measure_peaks
     mpeaks = measure_peaks(local)
     hbm = peaks.get("hbm_gbs")
@@ -488,6 +503,7 @@ def run_ours(args, rank, world, local):
             ref, t_or, cores = oracle_pass(w, ys, theta, rows)
             g, z = g32[name]
             errs[name] = {"grad_rel_err": float(np.linalg.norm(g[rows] - ref["g"]) / np.linalg.norm(ref["g"])),
+                          "worst_row_err": worst_row_err(g[rows], ref),
                           "z_rel_err": float(abs(z - ref["Z"]) / ref["Z"])}
             if name == "y0":
                 cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -529,16 +545,20 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world}", "generate_s": round(t_gen, 1),
                    "launch_shapes": {"walk_threads_per_block": walk_block, "attract_lanes_per_row": attract_lanes,
                                      "chosen_by": "--shapes" if args.shapes else "hts_autotune after the warm-up"}},
-        "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
-                     "fp32_mixed_ms_per_step_same_segment": ms32_seg / k64,
-                     "fp32_mixed_speedup": ms64 / ms32_seg},
-        "grad_rel_err": max((e["grad_rel_err"] for e in errs.values()), default=None),
-        "grad_error_gate": errs,
+        "kernel_rooflines": {"source": "the timed segment replayed with each phase timed alone (CUDA events)",
+                             "hbm_peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy, read + write)",
+                             "phase_ms_per_step": sphase, "kernels": kernels},
+        "measured_peaks": dict(mpeaks, note="this library's microbenchmarks (hts_measure_peaks), this run"),
         "phase_ms_per_step": {k: v / max(piters, 1) for k, v in prof.items()},
         "walk_counters_per_step": {"accepted_cells": acc / K, "leaf_pairs": pairs / K,
-                                   "warp_node_visits": visits / K,
+                                   "warp_node_visits": visits / K, "criterion_tests": crit / K,
                                    "interactions_per_point": (acc + pairs) / max(queries, 1),
                                    "replay_reproduced_trajectory": replay_same},
+        "y_end": {"max_radius": float(r_end.max()), "boundary_stop_would_fire": bool(np.any(r_end > 1 - 1e-4))},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
         "roofline": {"kernel": "walk_f32_kernel (BH tree walk)", "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "frac_of_measured_fp32": achieved / mpeaks["fp32_fma_tflops"]
@@ -546,15 +566,12 @@ def run_ours(args, rank, world, local):
                      "dominant_phase": dominant, "walk_ms": walk_ms,
                      "peak_basis": "FP32 lanes: %d SMs x 128 x 2 flop x %.0f MHz (sampled SM clock)" % (
                          props.multi_processor_count, sm_mhz)},
-        "cpu_baseline": cpu,
-        "kernel_rooflines": {"source": "the timed segment replayed with each phase timed alone (CUDA events)",
-                             "hbm_peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy, read + write)",
-                             "phase_ms_per_step": sphase, "kernels": kernels},
-        "measured_peaks": dict(mpeaks, note="this library's microbenchmarks (hts_measure_peaks), this run"),
-        "e2e": e2e,
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "y_end": {"max_radius": float(r_end.max()), "boundary_stop_would_fire": bool(np.any(r_end > 1 - 1e-4))},
+        # last, so that they stay in view when only the end of the line is kept
+        "fp64_gpu": {"value": value64, "unit": UNIT, "fp32_mixed_speedup": ms64 / ms32_seg, "steps": k64,
+                     "ms_per_step": ms64 / k64, "fp32_mixed_ms_per_step_same_segment": ms32_seg / k64},
+        "grad_error_gate": errs,
+        "grad_rel_err": max((e["grad_rel_err"] for e in errs.values()), default=None),
+        "grad_worst_row_err": max((e["worst_row_err"] for e in errs.values()), default=None),
     }
     print(json.dumps(line), flush=True)
 

@@ -201,6 +201,14 @@ HTS_API int hts_get_tree(hts_ctx *ctx, int64_t cap, int64_t *count_out, int32_t 
 HTS_API int hts_get_counters(hts_ctx *ctx, int64_t *out5);
 HTS_API int hts_set_counters(hts_ctx *ctx, int enable);
 
+/* Acceptance tests of Sec. 4.2 (r_cell / d < theta at an internal cell)
+ * made by the counted walks, one per (query point, cell) pair the walk
+ * reached with the point still open -- the criterion work itself, where
+ * warp node visits (hts_get_counters [2]) also count the lanes of a warp
+ * that had already accepted an ancestor.  Reset with the other counters.
+ * *out: host int64.  Errors: HTS_EINVAL, HTS_ECUDA. */
+HTS_API int hts_get_criterion_count(hts_ctx *ctx, int64_t *out);
+
 /* Per-phase timing.  While profiling is on, hts_step records CUDA events at
  * the phase boundaries of every iteration (up to 4096 per call).
  * hts_get_profile returns the accumulated milliseconds of the six phases --
@@ -314,15 +322,29 @@ HTS_API int hts_get_tuning(const hts_ctx *ctx, int *tuning);
  * Errors: HTS_EINVAL, HTS_ECUDA, HTS_EOOM. */
 HTS_API int hts_measure_peaks(int device, double *out3);
 
+/* Test of the bounded device-side waits (no counterpart in the paper).  The
+ * one-sweep sort passes (problems of more than 4096 points) wait, per tile,
+ * for the digit counts of earlier tiles; every such wait gives up after a
+ * bounded number of polls (~0.3 s), sets a status bit and writes no key out
+ * of range, so that a lost publication can never hang the GPU.  With
+ * spin_limit > 0 the first tile of every pass withholds its publication and
+ * the waits give up after spin_limit polls (microseconds): hts_step and
+ * hts_grad then return HTS_ETIMEOUT, and the failed iteration and the rest of
+ * that call leave Y, velocity and gains unchanged.  spin_limit = 0 (the
+ * default) restores normal operation; the context stays usable.  For tests
+ * only.  Errors: HTS_EINVAL (spin_limit outside [0, 4096]). */
+HTS_API int hts_set_wait_test(hts_ctx *ctx, int spin_limit);
+
 /* Number of points n and non-zeros nnz currently set (either may be NULL). */
 HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);
 
 /* ---- allocation-free exact gradient ---------------------------------------
- * The paper has no counterpart to this entry point; it is a service to
- * callers that must not allocate device memory -- code that queues work while
- * a CUDA graph is being captured, where cudaMalloc is not allowed, or a
- * plug-in inside a framework or server whose own allocator owns the device
- * memory budget.
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory: a plug-in inside a framework or inference
+ * server whose own allocator owns the device memory budget (a cudaMalloc
+ * behind its back can fail or starve it), or code on a latency-critical path
+ * that cannot take the implicit device synchronisation of cudaMalloc and
+ * cudaFree.
  *
  * hts_exact_grad_noalloc computes what hts_grad computes with theta = 0 in
  * HTS_FP64: g = 4 (exaggeration * F_attr - F_rep / Z) with the exact
@@ -330,9 +352,12 @@ HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);
  * device memory of the current device: y (n x 2 float64), the CSR matrix
  * (int64 indptr[n+1], int32 indices[nnz], float64 values[nnz], laid out as
  * for hts_set_P; not validated, but out-of-range entries are skipped), g_out
- * (n x 2 float64) and Z_out (one float64, may be NULL).  The work is queued
- * on `stream` (a cudaStream_t; NULL = legacy default stream) and is complete
- * in stream order; nothing is copied to the host.
+ * (n x 2 float64) and Z_out (one float64, may be NULL).  Every point must lie
+ * inside the open unit disk and be finite; the call does not read y back to
+ * the host to check, so a point outside gives NaN in every element of g_out
+ * and in *Z_out (the return value is still HTS_OK).  The work is queued on
+ * `stream` (a cudaStream_t; NULL = legacy default stream) and is complete in
+ * stream order; nothing is copied to the host.
  *
  * Work arrays live in one fixed file-scope device array sized for
  * HTS_NOALLOC_MAX_N points (about 4.5 MB); every device that loads the
@@ -341,10 +366,10 @@ HTS_API int hts_get_sizes(const hts_ctx *ctx, int64_t *n, int64_t *nnz);
  * made.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, which may make the driver load this library's
  * device code on that device); make that first call before any stream
- * capture.  All calls share the array and each call overwrites what it
- * reads, so no clearing is needed between calls -- but calls whose kernels
- * overlap on the GPU (other streams, other host threads on the same device)
- * race on it: serialise them.
+ * capture.  All calls share the array; each call clears the one flag that
+ * must start at zero and overwrites everything else it reads -- but calls
+ * whose kernels overlap on the GPU (other streams, other host threads on the
+ * same device) race on it: serialise them.
  * Errors: HTS_EINVAL (negative sizes, NULL pointers, bad grad_form or
  * exaggeration), HTS_ETOOLARGE, HTS_ECUDA (address lookup or launch failed). */
 #define HTS_NOALLOC_MAX_N 65536

@@ -39,7 +39,8 @@ EXPORTS = [
     "hts_set_counters", "hts_get_state", "hts_set_state", "hts_get_sizes", "hts_set_profiling",
     "hts_get_profile", "hts_exact_grad_noalloc", "hts_set_cosne", "hts_set_segments", "hts_get_segment_Z",
     "hts_kl_segments", "hts_set_graphs", "hts_autotune", "hts_set_tuning", "hts_get_tuning",
-    "hts_measure_peaks", "hts_set_walk_split", "hts_update_Y", "hts_get_walk_split",
+    "hts_measure_peaks", "hts_set_walk_split", "hts_update_Y", "hts_get_walk_split", "hts_get_criterion_count",
+    "hts_set_wait_test",
 ]
 MAX_SEGMENTS = 64
 
@@ -112,6 +113,8 @@ def load(path: str = LIB_PATH):
             "hts_set_walk_split": (i32, [vp, i32]),
             "hts_update_Y": (i32, [vp, vp, i32]),
             "hts_get_walk_split": (i32, [vp, vp]),
+            "hts_get_criterion_count": (i32, [vp, vp]),
+            "hts_set_wait_test": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

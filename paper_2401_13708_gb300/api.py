@@ -254,6 +254,13 @@ class HyperbolicTSNE:
         self._check(self._lib.hts_get_counters(self._ctx, out.ctypes.data_as(C.c_void_p)))
         return out
 
+    def criterion_count(self) -> int:
+        """Acceptance tests made by the counted walks (active lanes at internal
+        cells), reset by set_counters(True)."""
+        v = C.c_int64(0)
+        self._check(self._lib.hts_get_criterion_count(self._ctx, C.byref(v)))
+        return int(v.value)
+
     def set_profiling(self, enable: bool = True, serial: bool = False):
         """Per-phase CUDA-event timing; serial=True runs the attractive sum on
         the main stream so that every phase is timed alone."""

@@ -108,6 +108,7 @@ int ensure_points(hts_ctx *c, int64_t n)
     AL(c->radial, N);
     if (c->cfg.precision == HTS_FP32_MIXED) {
         AL(c->pts32, N);
+        AL(c->apts32, N);
         AL(c->spts32, N);
         AL(c->nodes32, 2 * N);
     } else {
@@ -136,6 +137,11 @@ int ensure_points(hts_ctx *c, int64_t n)
     AL(c->bn_sum, 6 * (N + 1));  // 3 x 128-bit fixed-point prefix sums (n + 1 entries, 48 B each)
     AL(c->cnt, N + 1);
     AL(c->pre, N + 1);
+    AL(c->walk_cost, (N + 31) / 32);       // one per walk block (at most one per warp)
+    AL(c->walk_order, (N + 31) / 32 + 1);
+    if (cudaMemset(c->walk_cost, 0, sizeof(unsigned) * ((N + 31) / 32)) != cudaSuccess ||
+        cudaMemset(c->walk_order, 0, sizeof(int) * ((N + 31) / 32 + 1)) != cudaSuccess)
+        return HTS_ECUDA;
     const int64_t tiles = ((int64_t)N + 4095) / 4096;
     AL(c->sort_scratch, (8 * 256 + 64) / 2 + sort_status_words((int64_t)N));
     c->scan_tmp_len = scan_tmp_size(std::max<int64_t>(256 * tiles, (int64_t)N + 1));
@@ -457,7 +463,7 @@ int hts_create(hts_ctx **out, const hts_config *cfg)
     }
     c->sm_count = prop.multiProcessorCount;
     if (dalloc(c, &c->minmax, 2 * kMaxSegments + 2) || dalloc(c, &c->dscal, 8) || dalloc(c, &c->status, 1) ||
-        dalloc(c, &c->counters, 4) || cudaMallocHost((void **)&c->h_pinned, 8 * sizeof(double)) != cudaSuccess) {
+        dalloc(c, &c->counters, 5) || cudaMallocHost((void **)&c->h_pinned, 8 * sizeof(double)) != cudaSuccess) {
         hts_destroy(c);
         return HTS_EOOM;
     }
@@ -472,7 +478,7 @@ int hts_create(hts_ctx **out, const hts_config *cfg)
         hts_destroy(c);
         return HTS_ECUDA;
     }
-    cudaMemset(c->counters, 0, 4 * sizeof(unsigned long long));
+    cudaMemset(c->counters, 0, 5 * sizeof(unsigned long long));
     cudaMemset(c->status, 0, sizeof(int));
     *out = c;
     return HTS_OK;
@@ -495,7 +501,7 @@ void hts_destroy(hts_ctx *c)
     dfree(&c->spts32); dfree(&c->spts64); dfree(&c->terms);
     dfree(&c->bn_left); dfree(&c->bn_right); dfree(&c->bn_parent); dfree(&c->leaf_parent);
     dfree(&c->bn_lo); dfree(&c->bn_hi); dfree(&c->bn_pref); dfree(&c->bn_flag); dfree(&c->bn_quad);
-    dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->nodes64);
+    dfree(&c->bn_sum); dfree(&c->cnt); dfree(&c->pre); dfree(&c->nodes32); dfree(&c->apts32); dfree(&c->walk_cost); dfree(&c->walk_order); dfree(&c->nodes64);
     dfree(&c->sort_scratch); dfree(&c->scan_tmp); dfree(&c->exact_part);
     if (c->split_part) cudaFree(c->split_part);
     if (c->split_frontier) cudaFree(c->split_frontier); dfree(&c->red_tmp); dfree(&c->minmax);
@@ -914,7 +920,7 @@ int hts_set_counters(hts_ctx *c, int enable)
     if (!c) return HTS_EINVAL;
     int r = set_device(c);
     if (r) return r;
-    if (enable && !c->counters_on) CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream));
+    if (enable && !c->counters_on) CK(cudaMemsetAsync(c->counters, 0, 5 * sizeof(unsigned long long), c->stream));
     c->counters_on = enable ? 1 : 0;
     c->layout_version += 1;
     return HTS_OK;
@@ -930,6 +936,27 @@ int hts_get_counters(hts_ctx *c, int64_t *out5)
     CK(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < 4; ++k) out5[k] = (int64_t)v[k];
     out5[4] = c->launches;
+    return HTS_OK;
+}
+
+int hts_set_wait_test(hts_ctx *c, int spin_limit)
+{
+    if (!c) return HTS_EINVAL;
+    if (spin_limit < 0 || spin_limit > 4096) return fail(c, HTS_EINVAL, "hts_set_wait_test: spin_limit in [0, 4096]");
+    c->wait_test = spin_limit;
+    c->layout_version += 1;  // captured graphs hold the sort's arguments
+    return HTS_OK;
+}
+
+int hts_get_criterion_count(hts_ctx *c, int64_t *out)
+{
+    if (!c || !out) return HTS_EINVAL;
+    int r = set_device(c);
+    if (r) return r;
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, c->counters + 4, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *out = (int64_t)v;
     return HTS_OK;
 }
 

@@ -4,11 +4,13 @@
 //
 // A group of lanes per row of P (8 in float32, a warp in float64) reads
 // consecutive (index, value) entries (coalesced), gathers the neighbours'
-// 32-byte point records (random, mostly L2 hits) and reduces three scalars
-// by shuffles.
+// point records (16-byte PointA in float32, 32-byte PointD in float64;
+// random, mostly L2 hits) and reduces three scalars by shuffles.
 // Per point: F_attr,i = 4 il_i (A_Delta + il_i A_s y_i) with
 //   A_Delta = sum_j p_ij (w d / t)_ij il_j Delta_ij,  A_s = same with s_ij.
-// Bytes per non-zero: 4 (index) + 4 or 8 (value) + 32 (gathered record).
+// Bytes per non-zero: 4 (index) + 4 or 8 (value) + 16 or 32 (gathered record).
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "hts_internal.cuh"
@@ -25,11 +27,19 @@ constexpr int kBlock = 256;
 constexpr int kUnroll = 4;
 constexpr int kAttractBlocksPerSM = 8;  // launch beside the walk: resident blocks per SM (0: full grid)
 
+// Lo floats of a PointA (see hts_internal.cuh): the packed halves times 2^-24.
+__device__ __forceinline__ float2 point_lo(unsigned lo)
+{
+    const float2 h = __half22float2(__halves2half2(__ushort_as_half((unsigned short)(lo & 0xFFFFu)),
+                                                   __ushort_as_half((unsigned short)(lo >> 16))));
+    return make_float2(h.x * 5.9604644775390625e-8f, h.y * 5.9604644775390625e-8f);
+}
+
 template <int GF, int kGroup>
 __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_t *__restrict__ indptr,
                                                              const int32_t *__restrict__ indices,
                                                              const float *__restrict__ vals,
-                                                             const PointF *__restrict__ pts, double2 *fattr)
+                                                             const PointA *__restrict__ pts, double2 *fattr)
 {
     // grid-stride over blocks of rows: one pass with the full grid, several
     // with the small grid of the background launch (kAttractBlocksPerSM)
@@ -39,7 +49,8 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
     const int lane = threadIdx.x & (kGroup - 1);
     const bool live = row < n;
     const int r = live ? row : n - 1;
-    const PointF q = pts[r];
+    const PointA q = pts[r];
+    const float2 ql = point_lo(q.lo);
     const float twoil = 2.0f * q.il;
     const int64_t e0 = indptr[r];
     const int len = live ? (int)(indptr[r + 1] - e0) : 0;  // a row is shorter than 2^31
@@ -56,16 +67,17 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
             j[u] = ok ? __ldg(ir + eu) : r;
             pv[u] = ok ? __ldg(vr + eu) : 0.0f;
         }
-        PointF o[kUnroll];
+        PointA o[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) o[u] = pts[j[u]];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            float dx = (q.xh - o[u].xh) + (q.xl - o[u].xl);
-            float dy = (q.yh - o[u].yh) + (q.yl - o[u].yl);
-            float s = fmaf(dx, dx, dy * dy);
-            PairF t = pair_terms_f32<GF>(s * twoil * o[u].il);
-            float k = pv[u] * t.att * o[u].il;
+            const float2 ol = point_lo(o[u].lo);
+            const float dx = (q.xh - o[u].xh) + (ql.x - ol.x);
+            const float dy = (q.yh - o[u].yh) + (ql.y - ol.y);
+            const float s = fmaf(dx, dx, dy * dy);
+            const PairF t = pair_terms_f32<GF>(s * twoil * o[u].il);
+            const float k = pv[u] * t.att * o[u].il;
             ax = fmaf(k, dx, ax);
             ay = fmaf(k, dy, ay);
             as = fmaf(k, s, as);
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
         as += __shfl_xor_sync(0xffffffffu, as, o);
     }
     if (lane == 0 && live) {
-        double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
+        double x = (double)q.xh + (double)ql.x, y = (double)q.yh + (double)ql.y;
         double il = (double)q.il;
         double asd = il * (double)as;
         fattr[row] = make_double2(4.0 * il * ((double)ax + asd * x), 4.0 * il * ((double)ay + asd * y));
@@ -295,7 +307,7 @@ void launch_attract(hts_ctx *c)
     if (c->cfg.precision == HTS_FP32_MIXED) {
         const float *v = (const float *)c->values;
 #define HTS_ATTRACT(GF, GG)                                                                             \
-    attract_f32_kernel<GF, GG><<<blocks32, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->pts32, \
+    attract_f32_kernel<GF, GG><<<blocks32, kBlock, 0, c->stream>>>(n, c->indptr, c->indices, v, c->apts32, \
                                                                     c->fattr)
 #define HTS_ATTRACT_G(GF)                          \
     switch (G) {                                   \

@@ -6,7 +6,8 @@
 // Per point (n), original order:  y, vel, gains (double2), fattr, frep
 //   (double2), zi (double), pts32 / pts64 (32-byte point records: position
 //   as float hi/lo pairs or double, and il = 1 / (1 - |y|^2) taken from
-//   float64), radial (double, split coordinate of the point).
+//   float64), apts32 (16-byte records of the float32 attractive sum),
+//   radial (double, split coordinate of the point).
 // Per point, key order:  keys / idx (uint64 / uint32, sort ping-pong),
 //   spts32 / spts64 (gathered records), terms (Einstein terms, 3 doubles).
 // Binary radix tree over the sorted keys (n - 1 internal nodes): children,
@@ -37,6 +38,17 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 struct __align__(16) PointF {
     float xh, yh, xl, yl;
     float il, pad0, pad1, pad2;
+};
+
+// Point record of the float32 attractive sum (16 bytes: the neighbour
+// gather moves half the bytes of a PointF): hi floats and il as in PointF,
+// and the lo floats scaled by 2^24 and rounded to half precision, packed in
+// one word (lo | hi << 16).  For |y| < 1 a lo float is at most 2^-25, so the
+// packed value is at most 0.5 and the position keeps an absolute error
+// below 2^-36 -- relative 1e-6 of a neighbour distance of 1e-5 at the rim.
+struct __align__(16) PointA {
+    float xh, yh, il;
+    unsigned lo;
 };
 
 // Point record, float64 mode.
@@ -109,6 +121,7 @@ struct hts_ctx {
     double2 *y = nullptr, *vel = nullptr, *gains = nullptr, *fattr = nullptr, *frep = nullptr;
     double *zi = nullptr, *radial = nullptr;
     hts::PointF *pts32 = nullptr;
+    hts::PointA *apts32 = nullptr;   // float32 attraction records
     hts::PointD *pts64 = nullptr;
 
     // per point, key order
@@ -137,7 +150,7 @@ struct hts_ctx {
     unsigned long long *minmax = nullptr;  // [2s] min bits, [2s+1] max bits of segment s; then the largest gamma
     double *dscal = nullptr;          // [0] Z, [1] sum p log p, [2] sum p log w, [3] sum p
     int *status = nullptr;
-    unsigned long long *counters = nullptr;  // 4
+    unsigned long long *counters = nullptr;  // 5: accepted cells, leaf pairs, warp visits, queries, criterion tests
     int *n_nodes = nullptr;          // device scalar: number of tree nodes
     double *h_pinned = nullptr;      // 8 doubles of pinned host scratch
 
@@ -163,12 +176,18 @@ struct hts_ctx {
     int attract_group = 8;           // float32 attraction lanes per row of P: 4, 8, 16 or 32
     int walk_split = -1;             // cut depth of the split walk (-1: by problem size)
     int attract_background = 0;      // set while the attraction is launched beside the walk
+    unsigned *walk_cost = nullptr;   // per walk block: cycles of the last walk (launch-order input)
+    int *walk_order = nullptr;       // [0] grid size, then the launch order of the walk's blocks
     void *split_frontier = nullptr;  // frontier table + entry count
     void *split_part = nullptr;      // partial sums of the split walk
 
     // CO-SNE term (Sec. 4.3): lambda1 KL + lambda2 (1/n) sum (|x|^2 - |y|^2)^2
     double cosne_l1 = 1.0, cosne_l2 = 0.0;
     double *xsq = nullptr;           // |x_i|^2, n doubles (nullptr: term off)
+
+    // wait test (hts_set_wait_test): > 0 = the look-back spin limit while the
+    // first tile of every sort pass withholds its status; 0 = off
+    int wait_test = 0;
 
     // instrumentation
     int64_t launches = 0;            // kernels launched since creation
@@ -281,8 +300,9 @@ __device__ __forceinline__ PairF pair_terms_f32(float delta)
     fs = fmaf(fs, delta, 1.0f);
     const float lg = __logf(1.0f + delta + t);
     const bool small = delta < 0.1f;
-    const float f = small ? fs : lg * rs;    // d / sinh(d)
-    const float d = small ? t * fs : lg;     // acosh(1 + delta)
+    const float2 ld = __fmul2_rn(make_float2(lg, t), make_float2(rs, fs));  // (lg / t, t fs): one paired multiply
+    const float f = small ? fs : ld.x;       // d / sinh(d)
+    const float d = small ? ld.y : lg;       // acosh(1 + delta)
     PairF p;
     p.w = __fdividef(1.0f, fmaf(d, d, 1.0f));
     if (GF == 0) {
@@ -293,6 +313,18 @@ __device__ __forceinline__ PairF pair_terms_f32(float delta)
         p.rep = p.w * p.att;
     }
     return p;
+}
+
+// Paired float32 arithmetic (one instruction for both components, each
+// rounded as the scalar operation): a - b and the compensated difference of
+// two hi/lo pairs, (ah - bh) + (al - bl) per component.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // -b + a, exact like a - b
+}
+__device__ __forceinline__ float2 delta2(float2 ah, float2 al, float2 bh, float2 bl)
+{
+    return __fadd2_rn(sub2(ah, bh), sub2(al, bl));
 }
 
 struct PairD {

@@ -12,6 +12,8 @@
 //   significant first), so that the depth-l cell of the equal-length tree is
 //   the top 2l key bits below the 6-bit segment id (bits 58..63).  The float64 steps use explicitly rounded
 //   intrinsics so no fused multiply-add changes a quantised bit.
+#include <cuda_fp16.h>
+
 #include "hts_internal.cuh"
 
 namespace hts {
@@ -32,8 +34,8 @@ __global__ void init_minmax_kernel(unsigned long long *mm, int nseg)
 // [min, max] of the radial coordinate (warp-reduced when a warp's points lie
 // in one segment, which is all but the warps straddling a boundary).
 __global__ void prep_points_kernel(int n, const double2 *__restrict__ y, int split_rule, PointF *pts32,
-                                   PointD *pts64, double *radial, const unsigned char *__restrict__ seg_of,
-                                   unsigned long long *mm)
+                                   PointA *apts32, PointD *pts64, double *radial,
+                                   const unsigned char *__restrict__ seg_of, unsigned long long *mm)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double c = 0.0;
@@ -52,6 +54,9 @@ __global__ void prep_points_kernel(int n, const double2 *__restrict__ y, int spl
             r.il = (float)il;
             r.pad0 = r.pad1 = r.pad2 = 0.f;
             pts32[i] = r;
+            const unsigned lx = __half_as_ushort(__float2half_rn(r.xl * 16777216.0f));  // lo * 2^24
+            const unsigned ly = __half_as_ushort(__float2half_rn(r.yl * 16777216.0f));
+            apts32[i] = PointA{r.xh, r.yh, r.il, lx | (ly << 16)};
         }
         if (pts64) pts64[i] = PointD{p.x, p.y, il, 0.0};
         c = split_rule == HTS_EQUAL_AREA ? __ddiv_rn(__dadd_rn(1.0, n2), __dsub_rn(1.0, n2)) : __dsqrt_rn(n2);
@@ -127,7 +132,8 @@ void launch_prep_points(hts_ctx *c)
     init_minmax_kernel<<<1, kMaxSegments, 0, c->stream>>>(c->minmax, c->nseg);
     bool f32 = c->cfg.precision == HTS_FP32_MIXED;
     prep_points_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(
-        n, c->y, c->cfg.split_rule, f32 ? c->pts32 : nullptr, f32 ? nullptr : c->pts64, c->radial,
+        n, c->y, c->cfg.split_rule, f32 ? c->pts32 : nullptr, f32 ? c->apts32 : nullptr, f32 ? nullptr : c->pts64,
+        c->radial,
         c->nseg > 1 ? c->seg_of : nullptr, c->minmax);
     c->launches += 2;
 }

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
                                                                 uint32_t *__restrict__ vout, int n, int shift,
                                                                 const int *__restrict__ digit_off,
                                                                 unsigned long long *tile_status, int *tile_ctr,
-                                                                int *status)
+                                                                int *status, int spin_limit, int withhold_first)
 {
     constexpr int kPerWarp = kTile / kWarps;
     constexpr int kRounds = kPerWarp / 32;
@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
         cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> mine(tile_status[(size_t)tile * 256 + d]);
         long long excl = 0;
         if (tile == 0) {
-            mine.store(kFlagPre | (unsigned long long)cnt, cuda::memory_order_relaxed);
+            // (withhold_first: the wait test of hts_set_wait_test; the later
+            // tiles' waits then run out)
+            if (!withhold_first) mine.store(kFlagPre | (unsigned long long)cnt, cuda::memory_order_relaxed);
         } else {
             mine.store(kFlagAgg | (unsigned long long)cnt, cuda::memory_order_relaxed);
             // decoupled look-back: add tile counts until an inclusive prefix
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
                     tile_status[(size_t)t * 256 + d]);
                 unsigned long long v = other.load(cuda::memory_order_relaxed);
                 int spins = 0;
-                while ((v >> 62) == 0ull && ++spins < kSpinLimit) {
+                while ((v >> 62) == 0ull && ++spins < spin_limit) {
                     __nanosleep(64);
                     v = other.load(cuda::memory_order_relaxed);
                 }
@@ -406,17 +408,19 @@ void launch_sort_pairs(hts_ctx *c)
     c->launches += 2 + kPasses;
     uint64_t *ka = c->keys, *kb = c->keys_alt;
     uint32_t *va = c->idx, *vb = c->idx_alt;
+    const int spin = c->wait_test > 0 ? c->wait_test : kSpinLimit;
+    const int hold = c->wait_test > 0 ? 1 : 0;
     for (int p = 0; p < kPasses; ++p) {
         unsigned long long *sp = stat + (size_t)p * 256 * tiles;
         if (tile == 1024)
             onesweep_kernel<1024><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
-                                                                         sp, ctr + p, c->status);
+                                                                         sp, ctr + p, c->status, spin, hold);
         else if (tile == 2048)
             onesweep_kernel<2048><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
-                                                                         sp, ctr + p, c->status);
+                                                                         sp, ctr + p, c->status, spin, hold);
         else
             onesweep_kernel<4096><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
-                                                                         sp, ctr + p, c->status);
+                                                                         sp, ctr + p, c->status, spin, hold);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }

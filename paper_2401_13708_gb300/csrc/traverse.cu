@@ -37,7 +37,7 @@ constexpr int kExactBlock = 64;
 __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int k)
 {
     const float4 *p = reinterpret_cast<const float4 *>(nodes + k);
-    float4 a = __ldg(p), b = __ldg(p + 1);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
     NodeF r;
     r.xh = a.x;
     r.yh = a.y;
@@ -68,6 +68,35 @@ __device__ __forceinline__ void segment_range(const SegView &sv, int p, int m, i
     end = min(sv.pre[sv.off[sg + 1]], m);
 }
 
+// Launch order of the walk's blocks.  A walk's chunks differ in cost (dense
+// regions have longer walks), and a grid of several waves whose costliest
+// blocks start last ends with a tail of few busy SMs.  Every walk therefore
+// records, per logical block, the cycles its warps took, and
+// walk_order_kernel turns them into the launch order of the next walk:
+// costliest first, the cheap blocks filling the end (longest-processing-time
+// first).  The mapping of chunks to warps is unchanged, so results do not
+// depend on the order.
+struct BlockOrder {
+    const int *order;  // [0]: grid size the order was made for; [1 + k]: logical block launched k-th
+    unsigned *cost;    // per logical block: summed cycles / 64 of its warps (nullptr: not recorded)
+};
+
+__device__ __forceinline__ int logical_block(const BlockOrder &bo)
+{
+    int b = blockIdx.x;
+    if (bo.order && bo.order[0] == (int)gridDim.x) {
+        const int o = bo.order[1 + blockIdx.x];
+        if (o >= 0 && o < (int)gridDim.x) b = o;
+    }
+    return b;
+}
+
+__device__ __forceinline__ void record_cost(const BlockOrder &bo, int b, long long t0)
+{
+    if (bo.cost && (threadIdx.x & 31) == 0)
+        atomicAdd(&bo.cost[b], (unsigned)min((clock64() - t0) >> 6, 0xFFFFFll));
+}
+
 // Split walk (small problems, one embedding): the root is never accepted
 // (every point lies inside it, and r_cell / d >= 1 > theta), so each point's
 // walk is the union of its walks of the subtrees below a cut of the tree at
@@ -96,26 +125,126 @@ struct SplitView {
     void *part;                       // [entry][n] partial sums (float4 / double4)
 };
 
+struct NodesF {  // float32 nodes: cell test and skip index
+    const NodeF *nodes;
+    __device__ bool cell(int k) const { return nodes[k].count >= 2.0f; }
+    __device__ int skip(int k) const { return nodes[k].skip; }
+};
+struct NodesD {  // float64 nodes
+    const NodeD *nodes;
+    __device__ bool cell(int k) const { return nodes[k].count >= 2; }
+    __device__ int skip(int k) const { return nodes[k].skip; }
+};
+
+// Per-lane state of the float32 walk: the query point (sorted position p),
+// its running sums, and the pre-order index from which the lane is open
+// again (a lane that accepts a cell skips the cell's subtree).
+struct LaneF {
+    float2 qh, ql;  // position as hi / lo float pairs
+    float twoil;
+    int p;
+    float2 rxy, rsz;  // sums of k Delta and of (k s, mult w)
+    int resume;
+    unsigned long long c_acc, c_pair, c_crit;  // counting walk only
+};
+
+// Adds mult times the pair term of (Delta, s, delta) with conformal factor il
+// of the other point: a cell's N_cell-weighted term (Eq. CellApproximation)
+// or one exact pair (mult = 1).
+// (The sums are paired: (rx, ry) += k Delta and (rs, z) += (k, mult) (s, w),
+// one fused multiply-add per pair, rounded as the scalar ones.)
+template <int GF>
+__device__ __forceinline__ void add_pair_f32(LaneF &L, float2 d, float s, float delta, float mult, float il)
+{
+    const PairF t = pair_terms_f32<GF>(delta);
+    const float k = mult * t.rep * il;
+    L.rxy = __ffma2_rn(make_float2(k, k), d, L.rxy);
+    L.rsz = __ffma2_rn(make_float2(k, mult), make_float2(s, t.w), L.rsz);
+}
+
+// The compensated difference y_i - y_j of two hi/lo float pairs and |y_i - y_j|^2.
+__device__ __forceinline__ float2 delta_f32(const LaneF &L, float2 h, float2 l, float &s)
+{
+    const float2 d = delta2(L.qh, L.ql, h, l);
+    s = fmaf(d.x, d.x, d.y * d.y);
+    return d;
+}
+
+// One visit of the warp's cursor at `node` (the node is the same for every
+// lane, so the branches on its kind are uniform).  Returns the next cursor:
+// at a cell, node + 1 if some open lane rejected it (the warp descends),
+// otherwise the index after its subtree; node + 1 after a leaf or bucket.
+template <int GF, bool COUNT, bool SEG>
+__device__ __forceinline__ int visit_f32(int node, int end, LaneF &L, const NodeF *__restrict__ nodes,
+                                         const PointF *__restrict__ spts, int n)
+{
+    const NodeF c = load_node(nodes, node);
+    const bool open = node >= L.resume && (!SEG || node < end);
+    int next = node + 1;
+    if (c.count >= 2) {  // cell: r_cell / d < theta  <=>  delta > thr
+        float s;
+        const float2 d = delta_f32(L, make_float2(c.xh, c.yh), make_float2(c.xl, c.yl), s);
+        const float delta = s * L.twoil * c.il;
+        const bool acc = open && delta > c.thr;
+        if (acc) {
+            add_pair_f32<GF>(L, d, s, delta, c.count, c.il);
+            L.resume = c.skip;
+        }
+        if (COUNT) {
+            L.c_crit += open ? 1 : 0;
+            L.c_acc += acc ? 1 : 0;
+        }
+        if (!__any_sync(0xffffffffu, open && !acc)) next = c.skip;
+    } else if (c.count == 1) {  // single-point leaf: the exact pair (not the lane's own point)
+        if (open && __float_as_int(c.thr) != L.p) {
+            float s;
+            const float2 d = delta_f32(L, make_float2(c.xh, c.yh), make_float2(c.xl, c.yl), s);
+            add_pair_f32<GF>(L, d, s, s * L.twoil * c.il, 1.0f, c.il);
+            if (COUNT) ++L.c_pair;
+        }
+    } else {  // depth-29 bucket: each of its points exactly
+        const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
+        if (open && lo >= 0 && cnt > 0 && lo + cnt <= n) {
+            for (int k2 = 0; k2 < cnt; ++k2) {
+                if (lo + k2 == L.p) continue;
+                const PointF o = spts[lo + k2];
+                float s;
+                const float2 d = delta_f32(L, make_float2(o.xh, o.yh), make_float2(o.xl, o.yl), s);
+                add_pair_f32<GF>(L, d, s, s * L.twoil * o.il, 1.0f, o.il);
+                if (COUNT) ++L.c_pair;
+            }
+        }
+    }
+    // next > node always: a cell's skip exceeds its position (emit writes no
+    // cell otherwise) and unwritten slots are zero (empty buckets)
+    return next;
+}
+
 // One warp walks for the 32 sorted points of chunk `warp` (and, split, the
 // frontier entry `fi`).
 template <int GF, bool COUNT, bool SEG, bool SPLIT>
 __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__restrict__ nodes,
-                                                const int *__restrict__ n_nodes,
-                                                const PointF *__restrict__ spts,
+                                                const int *__restrict__ n_nodes, const PointF *__restrict__ spts,
                                                 const uint32_t *__restrict__ idx, double2 *frep, double *zi,
                                                 unsigned long long *counters, const SegView sv,
                                                 const SplitView sp, int fi)
 {
     const int lane = threadIdx.x & 31;
-    const int p = warp * 32 + lane;
-    const bool valid = p < n;
-    const PointF q = spts[valid ? p : n - 1];
-    const float twoil = 2.0f * q.il;
-    float rx = 0.f, ry = 0.f, rs = 0.f, z = 0.f;
+    LaneF L;
+    L.p = warp * 32 + lane;
+    const bool valid = L.p < n;
+    {
+        const PointF q = spts[valid ? L.p : n - 1];
+        L.qh = make_float2(q.xh, q.yh);
+        L.ql = make_float2(q.xl, q.yl);
+        L.twoil = 2.0f * q.il;
+    }
+    L.rxy = L.rsz = make_float2(0.f, 0.f);
+    L.c_acc = L.c_pair = L.c_crit = 0;
+    unsigned long long c_visit = 0;
     const int m = min(*n_nodes, 2 * n);
     int root = 0, end = m;
-    if (SEG) segment_range(sv, valid ? p : n - 1, m, root, end);
-    unsigned long long c_acc = 0, c_pair = 0, c_visit = 0;
+    if (SEG) segment_range(sv, valid ? L.p : n - 1, m, root, end);
     bool live = valid;
     if (SPLIT) {  // frontier entry: ancestors first, then the subtree [node, skip)
         const Frontier F = sp.fr[fi];
@@ -123,20 +252,15 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
         for (int k = 0; k < kMaxSplitDepth; ++k) {
             if (k >= F.nanc) break;
             const NodeF a = load_node(nodes, F.anc[k]);
-            float dx = (q.xh - a.xh) + (q.xl - a.xl);
-            float dy = (q.yh - a.yh) + (q.yl - a.yl);
-            float s = fmaf(dx, dx, dy * dy);
-            float delta = s * twoil * a.il;
+            const bool own = (F.own >> k) & 1;
+            float s;
+            const float2 d = delta_f32(L, make_float2(a.xh, a.yh), make_float2(a.xl, a.yl), s);
+            const float delta = s * L.twoil * a.il;
+            if (COUNT) L.c_crit += (live && own) ? 1 : 0;
             if (live && delta > a.thr) {
-                if ((F.own >> k) & 1) {
-                    PairF t = pair_terms_f32<GF>(delta);
-                    float mult = (float)a.count;
-                    float kk = mult * t.rep * a.il;
-                    rx = fmaf(kk, dx, rx);
-                    ry = fmaf(kk, dy, ry);
-                    rs = fmaf(kk, s, rs);
-                    z = fmaf(mult, t.w, z);
-                    if (COUNT) ++c_acc;
+                if (own) {
+                    add_pair_f32<GF>(L, d, s, delta, a.count, a.il);
+                    if (COUNT) ++L.c_acc;
                 }
                 live = false;
             }
@@ -144,272 +268,47 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
         root = F.node;
         end = min(load_node(nodes, F.node).skip, m);
     }
-    int resume = live ? root : INT_MAX;
+    L.resume = live ? root : INT_MAX;
     int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : root;  // lane 0 holds the first segment
     const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : end;
-    // the loop body four times per trip: one loop-back branch per four node
-    // visits (4% fewer cycles than one visit per trip in this issue-bound loop)
+    // four visits per trip: one loop-back branch per four visits in this
+    // issue-bound loop
     while (node < stop) {
-        {
-        const NodeF c = load_node(nodes, node);
-        const bool active = node >= resume && (!SEG || node < end);
-        int next = node + 1;
-        if (c.count >= 2) {
-            float dx = (q.xh - c.xh) + (q.xl - c.xl);
-            float dy = (q.yh - c.yh) + (q.yl - c.yl);
-            float s = fmaf(dx, dx, dy * dy);
-            float delta = s * twoil * c.il;
-            bool acc = active && delta > c.thr;
-            if (acc) {
-                PairF t = pair_terms_f32<GF>(delta);
-                float mult = (float)c.count;
-                float k = mult * t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z = fmaf(mult, t.w, z);
-                resume = c.skip;
-                if (COUNT) ++c_acc;
-            }
-            if (!__any_sync(0xffffffffu, active && !acc)) next = c.skip;
-        } else if (c.count == 1) {
-            if (active && __float_as_int(c.thr) != p) {
-                float dx = (q.xh - c.xh) + (q.xl - c.xl);
-                float dy = (q.yh - c.yh) + (q.yl - c.yl);
-                float s = fmaf(dx, dx, dy * dy);
-                PairF t = pair_terms_f32<GF>(s * twoil * c.il);
-                float k = t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z += t.w;
-                if (COUNT) ++c_pair;
-            }
-        } else {
-            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
-            if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
-                for (int k2 = 0; k2 < cnt; ++k2) {
-                    if (lo + k2 == p) continue;
-                    PointF o = spts[lo + k2];
-                    float dx = (q.xh - o.xh) + (q.xl - o.xl);
-                    float dy = (q.yh - o.yh) + (q.yl - o.yl);
-                    float s = fmaf(dx, dx, dy * dy);
-                    PairF t = pair_terms_f32<GF>(s * twoil * o.il);
-                    float k = t.rep * o.il;
-                    rx = fmaf(k, dx, rx);
-                    ry = fmaf(k, dy, ry);
-                    rs = fmaf(k, s, rs);
-                    z += t.w;
-                    if (COUNT) ++c_pair;
-                }
-            }
-        }
+        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
         if (COUNT && lane == 0) ++c_visit;
-        // next > node always: a cell's skip exceeds its position (emit writes
-        // no cell otherwise) and unwritten slots are zero (empty buckets)
-        node = next;
-        }
         if (node >= stop) break;
-        {
-        const NodeF c = load_node(nodes, node);
-        const bool active = node >= resume && (!SEG || node < end);
-        int next = node + 1;
-        if (c.count >= 2) {
-            float dx = (q.xh - c.xh) + (q.xl - c.xl);
-            float dy = (q.yh - c.yh) + (q.yl - c.yl);
-            float s = fmaf(dx, dx, dy * dy);
-            float delta = s * twoil * c.il;
-            bool acc = active && delta > c.thr;
-            if (acc) {
-                PairF t = pair_terms_f32<GF>(delta);
-                float mult = (float)c.count;
-                float k = mult * t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z = fmaf(mult, t.w, z);
-                resume = c.skip;
-                if (COUNT) ++c_acc;
-            }
-            if (!__any_sync(0xffffffffu, active && !acc)) next = c.skip;
-        } else if (c.count == 1) {
-            if (active && __float_as_int(c.thr) != p) {
-                float dx = (q.xh - c.xh) + (q.xl - c.xl);
-                float dy = (q.yh - c.yh) + (q.yl - c.yl);
-                float s = fmaf(dx, dx, dy * dy);
-                PairF t = pair_terms_f32<GF>(s * twoil * c.il);
-                float k = t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z += t.w;
-                if (COUNT) ++c_pair;
-            }
-        } else {
-            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
-            if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
-                for (int k2 = 0; k2 < cnt; ++k2) {
-                    if (lo + k2 == p) continue;
-                    PointF o = spts[lo + k2];
-                    float dx = (q.xh - o.xh) + (q.xl - o.xl);
-                    float dy = (q.yh - o.yh) + (q.yl - o.yl);
-                    float s = fmaf(dx, dx, dy * dy);
-                    PairF t = pair_terms_f32<GF>(s * twoil * o.il);
-                    float k = t.rep * o.il;
-                    rx = fmaf(k, dx, rx);
-                    ry = fmaf(k, dy, ry);
-                    rs = fmaf(k, s, rs);
-                    z += t.w;
-                    if (COUNT) ++c_pair;
-                }
-            }
-        }
+        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
         if (COUNT && lane == 0) ++c_visit;
-        // next > node always: a cell's skip exceeds its position (emit writes
-        // no cell otherwise) and unwritten slots are zero (empty buckets)
-        node = next;
-        }
         if (node >= stop) break;
-        {
-        const NodeF c = load_node(nodes, node);
-        const bool active = node >= resume && (!SEG || node < end);
-        int next = node + 1;
-        if (c.count >= 2) {
-            float dx = (q.xh - c.xh) + (q.xl - c.xl);
-            float dy = (q.yh - c.yh) + (q.yl - c.yl);
-            float s = fmaf(dx, dx, dy * dy);
-            float delta = s * twoil * c.il;
-            bool acc = active && delta > c.thr;
-            if (acc) {
-                PairF t = pair_terms_f32<GF>(delta);
-                float mult = (float)c.count;
-                float k = mult * t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z = fmaf(mult, t.w, z);
-                resume = c.skip;
-                if (COUNT) ++c_acc;
-            }
-            if (!__any_sync(0xffffffffu, active && !acc)) next = c.skip;
-        } else if (c.count == 1) {
-            if (active && __float_as_int(c.thr) != p) {
-                float dx = (q.xh - c.xh) + (q.xl - c.xl);
-                float dy = (q.yh - c.yh) + (q.yl - c.yl);
-                float s = fmaf(dx, dx, dy * dy);
-                PairF t = pair_terms_f32<GF>(s * twoil * c.il);
-                float k = t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z += t.w;
-                if (COUNT) ++c_pair;
-            }
-        } else {
-            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
-            if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
-                for (int k2 = 0; k2 < cnt; ++k2) {
-                    if (lo + k2 == p) continue;
-                    PointF o = spts[lo + k2];
-                    float dx = (q.xh - o.xh) + (q.xl - o.xl);
-                    float dy = (q.yh - o.yh) + (q.yl - o.yl);
-                    float s = fmaf(dx, dx, dy * dy);
-                    PairF t = pair_terms_f32<GF>(s * twoil * o.il);
-                    float k = t.rep * o.il;
-                    rx = fmaf(k, dx, rx);
-                    ry = fmaf(k, dy, ry);
-                    rs = fmaf(k, s, rs);
-                    z += t.w;
-                    if (COUNT) ++c_pair;
-                }
-            }
-        }
+        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
         if (COUNT && lane == 0) ++c_visit;
-        // next > node always: a cell's skip exceeds its position (emit writes
-        // no cell otherwise) and unwritten slots are zero (empty buckets)
-        node = next;
-        }
         if (node >= stop) break;
-        {
-        const NodeF c = load_node(nodes, node);
-        const bool active = node >= resume && (!SEG || node < end);
-        int next = node + 1;
-        if (c.count >= 2) {
-            float dx = (q.xh - c.xh) + (q.xl - c.xl);
-            float dy = (q.yh - c.yh) + (q.yl - c.yl);
-            float s = fmaf(dx, dx, dy * dy);
-            float delta = s * twoil * c.il;
-            bool acc = active && delta > c.thr;
-            if (acc) {
-                PairF t = pair_terms_f32<GF>(delta);
-                float mult = (float)c.count;
-                float k = mult * t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z = fmaf(mult, t.w, z);
-                resume = c.skip;
-                if (COUNT) ++c_acc;
-            }
-            if (!__any_sync(0xffffffffu, active && !acc)) next = c.skip;
-        } else if (c.count == 1) {
-            if (active && __float_as_int(c.thr) != p) {
-                float dx = (q.xh - c.xh) + (q.xl - c.xl);
-                float dy = (q.yh - c.yh) + (q.yl - c.yl);
-                float s = fmaf(dx, dx, dy * dy);
-                PairF t = pair_terms_f32<GF>(s * twoil * c.il);
-                float k = t.rep * c.il;
-                rx = fmaf(k, dx, rx);
-                ry = fmaf(k, dy, ry);
-                rs = fmaf(k, s, rs);
-                z += t.w;
-                if (COUNT) ++c_pair;
-            }
-        } else {
-            const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
-            if (active && lo >= 0 && cnt > 0 && lo + cnt <= n) {
-                for (int k2 = 0; k2 < cnt; ++k2) {
-                    if (lo + k2 == p) continue;
-                    PointF o = spts[lo + k2];
-                    float dx = (q.xh - o.xh) + (q.xl - o.xl);
-                    float dy = (q.yh - o.yh) + (q.yl - o.yl);
-                    float s = fmaf(dx, dx, dy * dy);
-                    PairF t = pair_terms_f32<GF>(s * twoil * o.il);
-                    float k = t.rep * o.il;
-                    rx = fmaf(k, dx, rx);
-                    ry = fmaf(k, dy, ry);
-                    rs = fmaf(k, s, rs);
-                    z += t.w;
-                    if (COUNT) ++c_pair;
-                }
-            }
-        }
+        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
         if (COUNT && lane == 0) ++c_visit;
-        // next > node always: a cell's skip exceeds its position (emit writes
-        // no cell otherwise) and unwritten slots are zero (empty buckets)
-        node = next;
-        }
     }
     if (SPLIT && valid) {
-        reinterpret_cast<float4 *>(sp.part)[(size_t)fi * n + p] = make_float4(rx, ry, rs, z);
+        reinterpret_cast<float4 *>(sp.part)[(size_t)fi * n + L.p] = make_float4(L.rxy.x, L.rxy.y, L.rsz.x, L.rsz.y);
     } else if (valid) {
-        const uint32_t i = idx[p];
-        double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
-        double il = (double)q.il;
-        double rsd = il * (double)rs;
-        frep[i] = make_double2(4.0 * il * ((double)rx + rsd * x), 4.0 * il * ((double)ry + rsd * y));
-        zi[i] = (double)z;
+        const uint32_t i = idx[L.p];
+        double x = (double)L.qh.x + (double)L.ql.x, y = (double)L.qh.y + (double)L.ql.y;
+        double il = 0.5 * (double)L.twoil;
+        double rsd = il * (double)L.rsz.x;
+        frep[i] = make_double2(4.0 * il * ((double)L.rxy.x + rsd * x), 4.0 * il * ((double)L.rxy.y + rsd * y));
+        zi[i] = (double)L.rsz.y;
     }
     if (COUNT) {
+        unsigned long long c_acc = L.c_acc, c_pair = L.c_pair, c_crit = L.c_crit;
         for (int o = 16; o > 0; o >>= 1) {
             c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o);
             c_pair += __shfl_xor_sync(0xffffffffu, c_pair, o);
+            c_crit += __shfl_xor_sync(0xffffffffu, c_crit, o);
         }
         if (lane == 0) {
             atomicAdd(&counters[0], c_acc);
             atomicAdd(&counters[1], c_pair);
             atomicAdd(&counters[2], c_visit);
             atomicAdd(&counters[3], (unsigned long long)min(32, n - warp * 32));
+            atomicAdd(&counters[4], c_crit);
         }
     }
 }
@@ -418,17 +317,22 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
 // 32 <= kWalkBlock / 32, picked by the autotuner) take consecutive chunks, so
 // their walks share node data in L1.  The block size does not change results.
 template <int GF, bool COUNT, bool SEG, bool SPLIT>
-__global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodeF *__restrict__ nodes,
+__global__ void __launch_bounds__(kWalkBlock) walk_f32_kernel(int n, const NodesF nodes,
                                                               const int *__restrict__ n_nodes,
                                                               const PointF *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              const SegView sv, const SplitView sp)
+                                                              const SegView sv, const SplitView sp,
+                                                              const BlockOrder bo)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int b = logical_block(bo);
+    const int warp = (b * blockDim.x + threadIdx.x) >> 5;
     if (warp * 32 >= n) return;
     if (SPLIT && (int)blockIdx.y >= *sp.count) return;
-    walk_f32_chunk<GF, COUNT, SEG, SPLIT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv, sp, blockIdx.y);
+    const long long t0 = clock64();
+    walk_f32_chunk<GF, COUNT, SEG, SPLIT>(warp, n, nodes.nodes, n_nodes, spts, idx, frep, zi, counters, sv, sp,
+                                          blockIdx.y);
+    record_cost(bo, b, t0);
 }
 
 template <int GF, bool COUNT, bool SEG, bool SPLIT>
@@ -562,21 +466,62 @@ __global__ void __launch_bounds__(kWalkBlock) walk_f64_kernel(int n, const NodeD
                                                               const PointD *__restrict__ spts,
                                                               const uint32_t *__restrict__ idx, double2 *frep,
                                                               double *zi, unsigned long long *counters,
-                                                              const SegView sv, const SplitView sp)
+                                                              const SegView sv, const SplitView sp,
+                                                              const BlockOrder bo)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int b = logical_block(bo);
+    const int warp = (b * blockDim.x + threadIdx.x) >> 5;
     if (warp * 32 >= n) return;
     if (SPLIT && (int)blockIdx.y >= *sp.count) return;
+    const long long t0 = clock64();
     walk_f64_chunk<GF, COUNT, SEG, SPLIT>(warp, n, nodes, n_nodes, spts, idx, frep, zi, counters, sv, sp, blockIdx.y);
+    record_cost(bo, b, t0);
+}
+
+// The next launch order from the recorded costs: a counting sort on 256
+// levels of cost / (max + 1), costliest first (the order inside a level is
+// arbitrary); then the costs are cleared for the next walk.  One block.
+__global__ void __launch_bounds__(1024) walk_order_kernel(unsigned *cost, int nb, int *order)
+{
+    __shared__ unsigned hist[256];
+    __shared__ unsigned smax;
+    if (threadIdx.x < 256) hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) smax = 0;
+    __syncthreads();
+    unsigned m = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) m = max(m, cost[b]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&smax, m);
+    __syncthreads();
+    const unsigned long long top = (unsigned long long)smax + 1ull;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        atomicAdd(&hist[255 - (int)((unsigned long long)cost[b] * 256ull / top)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // exclusive scan over the 256 levels
+        unsigned run = 0;
+        for (int k = 0; k < 256; ++k) {
+            const unsigned h = hist[k];
+            hist[k] = run;
+            run += h;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const unsigned pos = atomicAdd(&hist[255 - (int)((unsigned long long)cost[b] * 256ull / top)], 1u);
+        order[1 + pos] = b;
+        cost[b] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) order[0] = nb;
 }
 
 // The frontier of the cut at `depth` (single thread; at most 4^depth entries
 // in pre-order).  A cell with more than 4 children or a skip that does not
 // advance is a broken tree: status bit 2, no entries (the walk then does no
 // work and the error is reported).
-template <typename NT>
-__global__ void frontier_kernel(const NT *__restrict__ nodes, const int *__restrict__ n_nodes, int n, int depth,
-                                Frontier *fr, int *count, int *status)
+template <typename NV>
+__global__ void frontier_kernel(const NV nodes, const int *__restrict__ n_nodes, int n, int depth, Frontier *fr,
+                                int *count, int *status)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int m = min(*n_nodes, 2 * n);
@@ -590,16 +535,15 @@ __global__ void frontier_kernel(const NT *__restrict__ nodes, const int *__restr
         int nb = 0;
         for (int e = 0; e < na && !bad; ++e) {
             const Frontier &E = a[e];
-            const NT c = nodes[E.node];
-            const int cnt = (int)c.count;
-            if (c.count < 2 || cnt < 2) {  // leaf or bucket: stays an entry
+            if (!nodes.cell(E.node)) {  // leaf or bucket: stays an entry
                 if (nb >= kMaxFrontier) { bad = true; break; }
                 b[nb++] = E;
                 continue;
             }
+            const int cskip = nodes.skip(E.node);
             bool first = true;
             int kids = 0;
-            for (int ch = E.node + 1; ch < c.skip && ch < m;) {
+            for (int ch = E.node + 1; ch < cskip && ch < m;) {
                 if (++kids > 4 || nb >= kMaxFrontier) { bad = true; break; }
                 Frontier F = E;
                 F.node = ch;
@@ -611,7 +555,7 @@ __global__ void frontier_kernel(const NT *__restrict__ nodes, const int *__restr
                 }
                 b[nb++] = F;
                 first = false;
-                const int nx = nodes[ch].skip;
+                const int nx = nodes.skip(ch);
                 if (nx <= ch) { bad = true; break; }
                 ch = nx;
             }
@@ -698,8 +642,9 @@ __global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(const PointF *__
     int jlo, jhi, cbeg, cend;
     exact_ranges(A, i, jlo, jhi, cbeg, cend);
     const PointF q = pts[i < n ? i : n - 1];
+    const float2 qh = make_float2(q.xh, q.yh), ql = make_float2(q.xl, q.yl);
     const float twoil = 2.0f * q.il;
-    float rx = 0.f, ry = 0.f, rs = 0.f, z = 0.f;
+    float2 rxy = make_float2(0.f, 0.f), rsz = make_float2(0.f, 0.f);  // paired sums, as in the walk
     for (int base = cbeg; base < cend; base += kExactBlock) {
         int j = base + threadIdx.x;
         if (j < cend) tile[threadIdx.x] = pts[j];
@@ -709,28 +654,25 @@ __global__ void __launch_bounds__(kExactBlock) exact_f32_kernel(const PointF *__
             const int jj = base + k;
             if (jj == i || jj < jlo || jj >= jhi) continue;
             const PointF o = tile[k];
-            float dx = (q.xh - o.xh) + (q.xl - o.xl);
-            float dy = (q.yh - o.yh) + (q.yl - o.yl);
-            float s = fmaf(dx, dx, dy * dy);
-            PairF t = pair_terms_f32<GF>(s * twoil * o.il);
-            float kk = t.rep * o.il;
-            rx = fmaf(kk, dx, rx);
-            ry = fmaf(kk, dy, ry);
-            rs = fmaf(kk, s, rs);
-            z += t.w;
+            const float2 d = delta2(qh, ql, make_float2(o.xh, o.yh), make_float2(o.xl, o.yl));
+            const float s = fmaf(d.x, d.x, d.y * d.y);
+            const PairF t = pair_terms_f32<GF>(s * twoil * o.il);
+            const float kk = t.rep * o.il;
+            rxy = __ffma2_rn(make_float2(kk, kk), d, rxy);
+            rsz = __ffma2_rn(make_float2(kk, 1.0f), make_float2(s, t.w), rsz);
         }
         __syncthreads();
     }
     if (i >= n) return;
     if (A.split > 1) {
-        A.part[(size_t)blockIdx.y * n + i] = make_double4_32a(rx, ry, rs, z);
+        A.part[(size_t)blockIdx.y * n + i] = make_double4_32a(rxy.x, rxy.y, rsz.x, rsz.y);
         return;
     }
     double x = (double)q.xh + (double)q.xl, y = (double)q.yh + (double)q.yl;
     double il = (double)q.il;
-    double rsd = il * (double)rs;
-    A.frep[i] = make_double2(4.0 * il * ((double)rx + rsd * x), 4.0 * il * ((double)ry + rsd * y));
-    A.zi[i] = (double)z;
+    double rsd = il * (double)rsz.x;
+    A.frep[i] = make_double2(4.0 * il * ((double)rxy.x + rsd * x), 4.0 * il * ((double)rxy.y + rsd * y));
+    A.zi[i] = (double)rsz.y;
 }
 
 template <int GF>
@@ -837,17 +779,21 @@ void launch_walk(hts_ctx *c)
         Frontier *fr = reinterpret_cast<Frontier *>(c->split_frontier);
         int *fcount = reinterpret_cast<int *>(fr + kMaxFrontier);
         if (c->cfg.precision == HTS_FP32_MIXED)
-            frontier_kernel<NodeF><<<1, 32, 0, c->stream>>>(c->nodes32, c->n_nodes, n, depth, fr, fcount, c->status);
+            frontier_kernel<<<1, 32, 0, c->stream>>>(NodesF{c->nodes32}, c->n_nodes, n, depth, fr, fcount, c->status);
         else
-            frontier_kernel<NodeD><<<1, 32, 0, c->stream>>>(c->nodes64, c->n_nodes, n, depth, fr, fcount, c->status);
+            frontier_kernel<<<1, 32, 0, c->stream>>>(NodesD{c->nodes64}, c->n_nodes, n, depth, fr, fcount, c->status);
         c->launches += 1;
         sp = SplitView{fr, fcount, c->split_part};
         grid.y = 1u << (2 * depth);
     }
     c->launches += 1;
+    // blocks in order of their cost in the previous walk, when the grid is
+    // more than one wave (resident threads per SM: 2048)
+    const bool balance = depth == 0 && (int64_t)grid.x > (int64_t)c->sm_count * (2048 / wb);
+    const BlockOrder bo{balance ? c->walk_order : nullptr, balance ? c->walk_cost : nullptr};
 #define HTS_WALK(P, NODES, SPTS, GF, CT, SG, SPL)                                                    \
     walk_##P##_kernel<GF, CT, SG, SPL><<<grid, wb, 0, c->stream>>>(n, NODES, c->n_nodes, SPTS, c->idx,   \
-                                                                   c->frep, c->zi, c->counters, sv, sp)
+                                                                   c->frep, c->zi, c->counters, sv, sp, bo)
 #define HTS_WALK_GF(P, NODES, SPTS, GF)                                                                   \
     if (depth > 0) {                                                                                       \
         if (cnt) HTS_WALK(P, NODES, SPTS, GF, true, false, true); else HTS_WALK(P, NODES, SPTS, GF, false, false, true); \
@@ -863,13 +809,18 @@ void launch_walk(hts_ctx *c)
         HTS_WALK_GF(P, NODES, SPTS, 1)                               \
     }
     if (c->cfg.precision == HTS_FP32_MIXED) {
-        HTS_WALK_ALL(f32, c->nodes32, c->spts32)
+        const NodesF nf{c->nodes32};
+        HTS_WALK_ALL(f32, nf, c->spts32)
     } else {
         HTS_WALK_ALL(f64, c->nodes64, c->spts64)
     }
 #undef HTS_WALK_ALL
 #undef HTS_WALK_GF
 #undef HTS_WALK
+    if (balance) {
+        walk_order_kernel<<<1, 1024, 0, c->stream>>>(c->walk_cost, (int)grid.x, c->walk_order);
+        c->launches += 1;
+    }
     if (depth > 0) {
         const int cb = (n + 255) / 256;
         const int *fcount = reinterpret_cast<const int *>(reinterpret_cast<Frontier *>(c->split_frontier) +

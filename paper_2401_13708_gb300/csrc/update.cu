@@ -22,6 +22,9 @@ namespace hts {
 namespace {
 
 constexpr int kBlock = 256;
+// status bits that void an iteration's gradient: tree node out of range (2),
+// sort position out of range (4), a bounded look-back wait ran out (128)
+constexpr int kStepBlockingStatus = 2 | 4 | 128;
 
 // Fixed-shape two-pass sum: kRedBlocks blocks reduce grid-strided slices,
 // one block adds the partials in order -- reproducible for a given n.
@@ -119,6 +122,10 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
     }
     if (A.g_out) A.g_out[i] = make_double2(gx, gy);
     if (!A.do_step) return;
+    // an iteration whose sort or tree build failed (a bounded wait ran out,
+    // a position or node out of range) leaves Y and the optimiser state as
+    // they were, so the context stays usable after the error is reported
+    if (*(volatile const int *)A.status & kStepBlockingStatus) return;
     double2 v = A.vel[i];
     const double a = 1.0 - n2;  // 2 / lambda (Eq. PoincareMetric)
     const double hl = 0.5 * a;  // 1 / lambda
