@@ -293,6 +293,21 @@ def cpu_model():
     return "unknown"
 
 
+def fp64_ops_record():
+    """FP64 FLOPs per point of the float64-bound phases, from the committed ncu
+    count (profiles/fp64_ops_step_n200k.txt), for the phases whose sources
+    still hash as recorded."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fp64_ops_step_n200k.txt")
+    if not os.path.exists(path):
+        return {}
+    rec = json.load(open(path))
+    csrc = os.path.join(ROOT, "paper_2401_13708_gb300", "csrc")
+    same = all(hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() == h
+               for f, h in rec.get("sources_sha256", {}).items())
+    return dict(rec["fp64_flop_per_point"]) if same else {}
+
+
 def worst_row_err(g, ref, exag=1.0):
     """max over rows of |g^_i - g_i| / (4 (exag |F_attr,i| + |F_rep,i| / Z)): each
     row's error against the size of the two force terms whose difference is g_i."""
@@ -435,11 +450,19 @@ def run_ours(args, rank, world, local):
     from paper_2401_13708_gb300 import measure_peaks
     mpeaks = measure_peaks(local)
     hbm = peaks.get("hbm_gbs")
+    fp64_rec = fp64_ops_record()
     kernels = {}
     for ph, bpp in BYTES_PER_POINT.items():
         gbs = bpp * n / (sphase[ph] * 1e-3) / 1e9
         kernels[ph] = {"bound": "hbm", "ms": sphase[ph], "algorithmic_bytes": bpp * n, "achieved": gbs,
                        "unit": "GB/s", "peak": hbm, "frac": gbs / hbm if hbm else None}
+        if ph in fp64_rec and mpeaks["fp64_fma_tflops"]:
+            # float64-pipe-bound phases: their FP64 rate against the measured FP64 FMA peak
+            tf = fp64_rec[ph] * n / (sphase[ph] * 1e-3) / 1e12
+            kernels[ph]["bound"] = "fp64"
+            kernels[ph]["fp64"] = {"flop_per_point": fp64_rec[ph], "achieved": tf, "unit": "TFLOP/s",
+                                   "peak": mpeaks["fp64_fma_tflops"], "frac": tf / mpeaks["fp64_fma_tflops"],
+                                   "peak_basis": "hts_measure_peaks float64 FMA, this run"}
     abytes = ATTRACT_BYTES_PER_NNZ * int(w.nnz) + ATTRACT_BYTES_PER_ROW * n
     agbs = abytes / (sphase["attract"] * 1e-3) / 1e9
     kernels["attract"] = {"bound": "hbm", "ms": sphase["attract"], "algorithmic_bytes": abytes, "achieved": agbs,
