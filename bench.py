@@ -56,6 +56,9 @@ def parse():
                     help="per-workload report (all five configurations) instead of the headline line")
     ap.add_argument("--workloads", default="gaussian_mixture,mnist_like,binary_tree,batched_mixtures,single_cell",
                     help="workloads of the --suite report")
+    ap.add_argument("--split-rule", default="both", choices=["equal_length", "equal_area", "both"],
+                    help="--suite: radial split rule(s) of the FP32-mixed runs at theta = 0.5; 'both' also "
+                         "reports the per-iteration time gain of equal-length over equal-area splits")
     ap.add_argument("--profile-only", action="store_true",
                     help="FP32-mixed steps only (for a profiler): no FP64 arm, e2e or oracle")
     return ap.parse_args()
@@ -622,8 +625,9 @@ def run_suite(args, rank, world, local):
     def schedule(n_total, ee, exag, mom1, mom2, lr):
         return [(ee, exag, lr, mom1), (n_total - ee, 1.0, lr, mom2)]
 
-    def gpu_time(prec, w, y0, sched, theta, max_iters=None, segments=None, lr_scale=None, graphs=False):
-        t = HyperbolicTSNE(precision=prec, device=local)
+    def gpu_time(prec, w, y0, sched, theta, max_iters=None, segments=None, lr_scale=None, graphs=False,
+                 split_rule="equal_length"):
+        t = HyperbolicTSNE(precision=prec, device=local, split_rule=split_rule)
         t.set_P(w.indptr, w.indices, w.values)
         t.set_Y(y0)
         if segments is not None:
@@ -694,7 +698,19 @@ def run_suite(args, rank, world, local):
             line = {"workload": inputs.WORKLOADS[name], "n": w.n, "nnz": w.nnz, "theta": theta,
                     "iterations": 1000,
                     "schedule": "250 x (exaggeration 12, momentum 0.5) + 750 x (1, 0.8), lr = N/12000"}
-            line["fp32_mixed_gpu"] = gpu_time("fp32", w, w.y0, sched, theta)
+            if args.split_rule != "equal_area":
+                line["fp32_mixed_gpu"] = gpu_time("fp32", w, w.y0, sched, theta)
+            if theta == 0.5 and args.split_rule != "equal_length":
+                # Sec. 5.2.2 (Time Gain by Splitting Choices): the same run on equal-area splits
+                line["fp32_mixed_gpu_equal_area"] = gpu_time("fp32", w, w.y0, sched, theta, split_rule="equal_area")
+                if "fp32_mixed_gpu" in line:
+                    t_len = 1.0 / line["fp32_mixed_gpu"]["iters_per_s"]
+                    t_area = 1.0 / line["fp32_mixed_gpu_equal_area"]["iters_per_s"]
+                    line["equal_length_time_gain"] = {"per_iteration": 1.0 - t_len / t_area,
+                                                      "note": "1 - t(equal length) / t(equal area), FP32-mixed"}
+            if args.split_rule == "equal_area":
+                emit(line)
+                continue
             f64 = gpu_time("fp64", w, w.y0, sched, theta, max_iters=60 if name == "single_cell" else 250)
             line["fp64_gpu"] = f64
             f32p = gpu_time("fp32", w, w.y0, sched, theta, max_iters=f64["timed_iters"])
