@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--split-rule", default="both", choices=["equal_length", "equal_area", "both"],
                     help="--suite: radial split rule(s) of the FP32-mixed runs at theta = 0.5; 'both' also "
                          "reports the per-iteration time gain of equal-length over equal-area splits")
+    ap.add_argument("--save-y", default="", help="--profile-only: save Y after the warm-up (.npy)")
+    ap.add_argument("--load-y", default="",
+                    help="--profile-only: start from this Y (.npy, e.g. from --save-y) instead of running the "
+                         "warm-up iterations (a profiler then sees few launches before the timed ones)")
     ap.add_argument("--profile-only", action="store_true",
                     help="FP32-mixed steps only (for a profiler): no FP64 arm, e2e or oracle")
     return ap.parse_args()
@@ -361,7 +365,12 @@ def run_ours(args, rank, world, local):
         t.set_Y(ys)
         g32[name] = t.grad(theta, 1.0)
     t.set_Y(y0)
-    protocol(t, 0, W, theta, lr)
+    if args.profile_only and args.load_y:          # a saved state stands in for the warm-up
+        t.set_Y(np.load(args.load_y))
+    else:
+        protocol(t, 0, W, theta, lr)
+    if args.profile_only and args.save_y:
+        np.save(args.save_y, t.get_Y())
     if args.shapes:                                # fixed launch shapes (e.g. for a profiler run)
         t.set_tuning(*[int(v) for v in args.shapes.split(",")])
         walk_block, attract_lanes = t.get_tuning()
