@@ -110,7 +110,7 @@ int ensure_points(hts_ctx *c, int64_t n)
         AL(c->pts32, N);
         AL(c->apts32, N);
         AL(c->spts32, N);
-        AL(c->nodes32, 2 * N);
+        AL(c->nodes32, 2 * N + kWalkOverrun);
     } else {
         AL(c->pts64, N);
         AL(c->spts64, N);
@@ -118,7 +118,8 @@ int ensure_points(hts_ctx *c, int64_t n)
     }
     // a node slot never written by a tree build reads as an empty bucket
     // (count 0), which the walk steps over
-    if (c->nodes32 && cudaMemset(c->nodes32, 0, sizeof(NodeF) * 2 * N) != cudaSuccess) return HTS_ECUDA;
+    if (c->nodes32 && cudaMemset(c->nodes32, 0, sizeof(NodeF) * (2 * N + kWalkOverrun)) != cudaSuccess)
+        return HTS_ECUDA;
     if (c->nodes64 && cudaMemset(c->nodes64, 0, sizeof(NodeD) * 2 * N) != cudaSuccess) return HTS_ECUDA;
     AL(c->keys, N);
     AL(c->keys_alt, N);
@@ -192,13 +193,15 @@ int status_error(hts_ctx *c, int st)
 constexpr int kPhases = 6;  // keys, sort, tree, walk/exact, attract, Z + update
 constexpr int kEvents = kPhases + 3;  // per iteration: 6 marks on the main stream, 2 on the side stream
 constexpr int kMaxSplitCut = 3;      // deepest cut the autotuner tries (hts_set_walk_split's range)
-constexpr int kAttractAfter = 3;      // stage after which the attraction forks: 0 prep, 1 keys, 2 sort, 3 tree
+// stage after which the attraction forks (0 prep, 1 keys, 2 sort, 3 tree):
+// float32 after the sort, float64 (a heavier attraction) after the tree build
+constexpr int kAttractAfter32 = 2, kAttractAfter64 = 3;
 
 // Repulsion, attraction and Z for the current Y (results in frep, zi, fattr,
 // dscal[0] / seg_z).  The attractive sum needs only the point records, so it
-// runs on the side stream (lowest priority) from the stage kAttractAfter to
-// the Z reduction, as a small resident grid beside the walk (see
-// launch_attract).  With `ev` (kEvents events)
+// runs on the side stream (lowest priority) from the stage kAttractAfter32 /
+// kAttractAfter64 to the Z reduction, as a small resident grid beside the
+// latency-bound tree build and the walk (see launch_attract).  With `ev` (kEvents events)
 // the stage boundaries are recorded: ev[0..4] and ev[6] on the main stream
 // (start, after keys, sort, tree, walk / exact; ev[6] after the update is
 // recorded by the caller), ev[7..8] around the attractive sum.
@@ -210,8 +213,9 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
     // by itself, and an attraction beside it only lengthens its tail
     const bool serial = c->profiling == 2 || theta == 0.0;
     const bool attract = c->nnz > 0 && !serial;
+    const int fork_at = c->cfg.precision == HTS_FP32_MIXED ? kAttractAfter32 : kAttractAfter64;
     // fork: the side stream waits for the point records (and for the stages
-    // before kAttractAfter, so that it does not hold SMs they need)
+    // before fork_at, so that it does not hold SMs they need)
     auto fork_attract = [&]() -> int {
         CK(cudaEventRecord(c->aev_fork, c->stream));
         CK(cudaStreamWaitEvent(c->astream, c->aev_fork, 0));
@@ -239,19 +243,19 @@ int run_gradient(hts_ctx *c, double theta, cudaEvent_t *ev = nullptr)
         launch_exact(c);
         LAUNCHED("exact");
     } else {
-        if (attract && kAttractAfter == 0 && (r = fork_attract())) return r;
+        if (attract && fork_at == 0 && (r = fork_attract())) return r;
         launch_make_keys(c);
         LAUNCHED("make_keys");
         MARK(1);
-        if (attract && kAttractAfter == 1 && (r = fork_attract())) return r;
+        if (attract && fork_at == 1 && (r = fork_attract())) return r;
         launch_sort_pairs(c);
         LAUNCHED("sort");
         MARK(2);
-        if (attract && kAttractAfter == 2 && (r = fork_attract())) return r;
+        if (attract && fork_at == 2 && (r = fork_attract())) return r;
         launch_build_tree(c, theta, nullptr);
         LAUNCHED("build_tree");
         MARK(3);
-        if (attract && kAttractAfter == 3 && (r = fork_attract())) return r;
+        if (attract && fork_at == 3 && (r = fork_attract())) return r;
         launch_walk(c);
         LAUNCHED("walk");
     }

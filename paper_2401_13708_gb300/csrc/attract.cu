@@ -25,7 +25,9 @@ constexpr int kBlock = 256;
 // leave most of a warp idle; each lane keeps kUnroll index loads and gathers
 // in flight before its arithmetic.
 constexpr int kUnroll = 4;
-constexpr int kAttractBlocksPerSM = 8;  // launch beside the walk: resident blocks per SM (0: full grid)
+// launched in the background: resident blocks per SM of the float32 (beside the
+// tree build and the walk) and float64 (beside the walk) attraction
+constexpr int kAttractBlocksPerSM32 = 2, kAttractBlocksPerSM64 = 8;
 
 // Lo floats of a PointA (see hts_internal.cuh): the packed halves times 2^-24.
 __device__ __forceinline__ float2 point_lo(unsigned lo)
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(kBlock) attract_f32_kernel(int n, const int64_
                                                              const PointA *__restrict__ pts, double2 *fattr)
 {
     // grid-stride over blocks of rows: one pass with the full grid, several
-    // with the small grid of the background launch (kAttractBlocksPerSM)
+    // with the small grid of the background launch (kAttractBlocksPerSM32)
     const int64_t span = (int64_t)n * kGroup;
     for (int64_t base = (int64_t)blockIdx.x * kBlock; base < span; base += (int64_t)gridDim.x * kBlock) {
     const int row = (int)((base + threadIdx.x) / kGroup);
@@ -294,15 +296,11 @@ void launch_attract(hts_ctx *c)
     const int n = (int)c->n;
     const int blocks = (int)(((int64_t)n * 32 + kBlock - 1) / kBlock);
     const int G = c->attract_group;
-    // kAttractBlocksPerSM > 0: a small resident grid that strides over the rows
-    // in the background of the walk instead of one block per 256 / G rows
+    // in the background: a small resident grid that strides over the rows
+    // instead of one block per 256 / G rows
     const int full = (int)(((int64_t)n * G + kBlock - 1) / kBlock);
-    const int blocks32 = kAttractBlocksPerSM > 0 && c->attract_background
-                             ? std::min(full, kAttractBlocksPerSM * c->sm_count)
-                             : full;
-    const int blocks64 = kAttractBlocksPerSM > 0 && c->attract_background
-                             ? std::min(blocks, kAttractBlocksPerSM * c->sm_count)
-                             : blocks;
+    const int blocks32 = c->attract_background ? std::min(full, kAttractBlocksPerSM32 * c->sm_count) : full;
+    const int blocks64 = c->attract_background ? std::min(blocks, kAttractBlocksPerSM64 * c->sm_count) : blocks;
     c->launches += 1;
     if (c->cfg.precision == HTS_FP32_MIXED) {
         const float *v = (const float *)c->values;

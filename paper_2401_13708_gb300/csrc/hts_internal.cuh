@@ -72,6 +72,9 @@ struct __align__(16) NodeF {
     float count;
     int skip;
 };
+// Empty float32 node slots the tree build writes after its last node (the
+// walk visits up to three past its last node: four visits per loop test).
+constexpr int kWalkOverrun = 4;
 
 // Tree node, float64 mode (same meaning; pos = sorted position for leaves
 // and buckets).

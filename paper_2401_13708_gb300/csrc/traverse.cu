@@ -34,11 +34,24 @@ namespace {
 constexpr int kWalkBlock = 256;
 constexpr int kExactBlock = 64;
 
+#ifndef HTS_NODE_LOAD256
+#define HTS_NODE_LOAD256 0
+#endif
+// One node, read through the non-coherent path: a single 256-bit load (the
+// node array comes from cudaMalloc and a node is 32 bytes, so every node is
+// 32-byte aligned).
 __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int k)
 {
+    NodeF r;
+#if HTS_NODE_LOAD256
+    float skipf;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r.xh), "=f"(r.yh), "=f"(r.xl), "=f"(r.yl), "=f"(r.il), "=f"(r.thr), "=f"(r.count), "=f"(skipf)
+        : "l"(nodes + k));
+    r.skip = __float_as_int(skipf);
+#else
     const float4 *p = reinterpret_cast<const float4 *>(nodes + k);
     const float4 a = __ldg(p), b = __ldg(p + 1);
-    NodeF r;
     r.xh = a.x;
     r.yh = a.y;
     r.xl = a.z;
@@ -47,6 +60,7 @@ __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int 
     r.thr = b.y;
     r.count = b.z;
     r.skip = __float_as_int(b.w);
+#endif
     return r;
 }
 
@@ -174,12 +188,13 @@ __device__ __forceinline__ float2 delta_f32(const LaneF &L, float2 h, float2 l, 
 // lane, so the branches on its kind are uniform).  Returns the next cursor:
 // at a cell, node + 1 if some open lane rejected it (the warp descends),
 // otherwise the index after its subtree; node + 1 after a leaf or bucket.
-template <int GF, bool COUNT, bool SEG>
+// BOUNDED: a lane is open only below its own `end` (segments, split walk).
+template <int GF, bool COUNT, bool BOUNDED>
 __device__ __forceinline__ int visit_f32(int node, int end, LaneF &L, const NodeF *__restrict__ nodes,
                                          const PointF *__restrict__ spts, int n)
 {
     const NodeF c = load_node(nodes, node);
-    const bool open = node >= L.resume && (!SEG || node < end);
+    const bool open = node >= L.resume && (!BOUNDED || node < end);
     int next = node + 1;
     if (c.count >= 2) {  // cell: r_cell / d < theta  <=>  delta > thr
         float s;
@@ -271,20 +286,21 @@ __device__ __forceinline__ void walk_f32_chunk(int warp, int n, const NodeF *__r
     L.resume = live ? root : INT_MAX;
     int node = SEG ? __shfl_sync(0xffffffffu, root, 0) : root;  // lane 0 holds the first segment
     const int stop = SEG ? __reduce_max_sync(0xffffffffu, valid ? end : 0) : end;
-    // four visits per trip: one loop-back branch per four visits in this
-    // issue-bound loop
+    // four visits per trip and one test of the cursor: in this issue-bound
+    // loop the loop-back branch and the cursor tests cost.  The cursor may run
+    // up to three nodes past `stop`: past the last node the tree build leaves
+    // four empty slots (visited as no-ops), and below it every lane's own
+    // bound `end` closes it (BOUNDED).
+    constexpr bool kBounded = SEG || SPLIT;
     while (node < stop) {
-        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
-        if (COUNT && lane == 0) ++c_visit;
-        if (node >= stop) break;
-        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
-        if (COUNT && lane == 0) ++c_visit;
-        if (node >= stop) break;
-        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
-        if (COUNT && lane == 0) ++c_visit;
-        if (node >= stop) break;
-        node = visit_f32<GF, COUNT, SEG>(node, end, L, nodes, spts, n);
-        if (COUNT && lane == 0) ++c_visit;
+        if (COUNT && lane == 0) ++c_visit;  // (counted: visits below stop)
+        node = visit_f32<GF, COUNT, kBounded>(node, end, L, nodes, spts, n);
+        if (COUNT && lane == 0 && node < stop) ++c_visit;
+        node = visit_f32<GF, COUNT, kBounded>(node, end, L, nodes, spts, n);
+        if (COUNT && lane == 0 && node < stop) ++c_visit;
+        node = visit_f32<GF, COUNT, kBounded>(node, end, L, nodes, spts, n);
+        if (COUNT && lane == 0 && node < stop) ++c_visit;
+        node = visit_f32<GF, COUNT, kBounded>(node, end, L, nodes, spts, n);
     }
     if (SPLIT && valid) {
         reinterpret_cast<float4 *>(sp.part)[(size_t)fi * n + L.p] = make_float4(L.rxy.x, L.rxy.y, L.rsz.x, L.rsz.y);

@@ -425,6 +425,10 @@ __global__ void emit_kernel(EmitArgs A)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = A.n;
+    if (k == 0 && A.nodes32) {  // four empty slots after the last node: the float32 walk's overrun
+        const int m = min(A.pre[n], A.capacity);
+        for (int e = 0; e < kWalkOverrun; ++e) A.nodes32[m + e] = NodeF{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    }
     if (k < n - 1 && A.quad[k]) {
         int lo = A.lo_arr[k], hi = A.hi_arr[k];
         int ell = quad_level(A.pref[k]);
