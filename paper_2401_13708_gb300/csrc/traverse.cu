@@ -34,33 +34,17 @@ namespace {
 constexpr int kWalkBlock = 256;
 constexpr int kExactBlock = 64;
 
-#ifndef HTS_NODE_LOAD256
-#define HTS_NODE_LOAD256 0
-#endif
 // One node, read through the non-coherent path: a single 256-bit load (the
 // node array comes from cudaMalloc and a node is 32 bytes, so every node is
-// 32-byte aligned).
+// 32-byte aligned); two 128-bit loads measured 2% slower.
 __device__ __forceinline__ NodeF load_node(const NodeF *__restrict__ nodes, int k)
 {
     NodeF r;
-#if HTS_NODE_LOAD256
     float skipf;
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(r.xh), "=f"(r.yh), "=f"(r.xl), "=f"(r.yl), "=f"(r.il), "=f"(r.thr), "=f"(r.count), "=f"(skipf)
         : "l"(nodes + k));
     r.skip = __float_as_int(skipf);
-#else
-    const float4 *p = reinterpret_cast<const float4 *>(nodes + k);
-    const float4 a = __ldg(p), b = __ldg(p + 1);
-    r.xh = a.x;
-    r.yh = a.y;
-    r.xl = a.z;
-    r.yl = a.w;
-    r.il = b.x;
-    r.thr = b.y;
-    r.count = b.z;
-    r.skip = __float_as_int(b.w);
-#endif
     return r;
 }
 
@@ -201,9 +185,12 @@ __device__ __forceinline__ int visit_f32(int node, int end, LaneF &L, const Node
         const float2 d = delta_f32(L, make_float2(c.xh, c.yh), make_float2(c.xl, c.yl), s);
         const float delta = s * L.twoil * c.il;
         const bool acc = open && delta > c.thr;
-        if (acc) {
-            add_pair_f32<GF>(L, d, s, delta, c.count, c.il);
-            L.resume = c.skip;
+        // the pair term runs on every lane when one accepts (no divergent
+        // branch); a lane that rejects adds it with weight 0, which leaves its
+        // sums unchanged (every term is finite: delta is clamped)
+        if (__any_sync(0xffffffffu, acc)) {
+            add_pair_f32<GF>(L, d, s, delta, acc ? c.count : 0.0f, c.il);
+            L.resume = acc ? c.skip : L.resume;
         }
         if (COUNT) {
             L.c_crit += open ? 1 : 0;
@@ -211,11 +198,12 @@ __device__ __forceinline__ int visit_f32(int node, int end, LaneF &L, const Node
         }
         if (!__any_sync(0xffffffffu, open && !acc)) next = c.skip;
     } else if (c.count == 1) {  // single-point leaf: the exact pair (not the lane's own point)
-        if (open && __float_as_int(c.thr) != L.p) {
+        const bool take = open && __float_as_int(c.thr) != L.p;
+        if (__any_sync(0xffffffffu, take)) {  // as at a cell: weight 0 for the other lanes
             float s;
             const float2 d = delta_f32(L, make_float2(c.xh, c.yh), make_float2(c.xl, c.yl), s);
-            add_pair_f32<GF>(L, d, s, s * L.twoil * c.il, 1.0f, c.il);
-            if (COUNT) ++L.c_pair;
+            add_pair_f32<GF>(L, d, s, s * L.twoil * c.il, take ? 1.0f : 0.0f, c.il);
+            if (COUNT) L.c_pair += take ? 1 : 0;
         }
     } else {  // depth-29 bucket: each of its points exactly
         const int lo = __float_as_int(c.thr), cnt = (int)(-c.count);
