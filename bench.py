@@ -302,17 +302,20 @@ def cpu_model():
 
 def fp64_ops_record():
     """FP64 FLOPs per point of the float64-bound phases, from the committed ncu
-    count (profiles/fp64_ops_step_n200k.txt), for the phases whose sources
-    still hash as recorded."""
+    count (profiles/fp64_ops_step_n200k.txt), for each phase whose kernel
+    source still hashes as recorded."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "fp64_ops_step_n200k.txt")
     if not os.path.exists(path):
         return {}
     rec = json.load(open(path))
     csrc = os.path.join(ROOT, "paper_2401_13708_gb300", "csrc")
-    same = all(hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() == h
-               for f, h in rec.get("sources_sha256", {}).items())
-    return dict(rec["fp64_flop_per_point"]) if same else {}
+    out = {}
+    for ph, flop in rec["fp64_flop_per_point"].items():
+        f = rec["phase_source"][ph]
+        if hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() == rec["sources_sha256"][f]:
+            out[ph] = flop
+    return out
 
 
 def worst_row_err(g, ref, exag=1.0):
