@@ -304,7 +304,7 @@ HTS_API int hts_autotune(hts_ctx *ctx, double theta, int reps, int *tuning);
  * exactly the interactions of its own walk (the partial sums are added in a
  * fixed order).  depth = -1 (default) picks the shallowest cut that gives
  * about 2048 warps, within a partial-sum buffer of
- * min(64 n, 2^22) entries for n <= 262144 (no split above).  Errors: HTS_EINVAL (depth < -1 or > 3). */
+ * min(64 n, 2^22) entries for n <= 524288 (no split above).  Errors: HTS_EINVAL (depth < -1 or > 3). */
 HTS_API int hts_set_walk_split(hts_ctx *ctx, int depth);
 /* The cut depth in use (the automatic choice resolved; 0 with segments).
  * hts_autotune also times every depth the buffer allows on the current

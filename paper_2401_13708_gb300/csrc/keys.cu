@@ -44,21 +44,20 @@ __global__ void prep_points_kernel(int n, const double2 *__restrict__ y, int spl
     if (ok) {
         double2 p = y[i];
         double n2 = __dadd_rn(__dmul_rn(p.x, p.x), __dmul_rn(p.y, p.y));
-        double il = __ddiv_rn(1.0, __dsub_rn(1.0, n2));
-        if (pts32) {
+        if (pts32) {  // il as the float reciprocal of 1 - |y|^2 (off the float64 pipe)
             PointF r;
             r.xh = (float)p.x;
             r.yh = (float)p.y;
             r.xl = (float)(p.x - (double)r.xh);
             r.yl = (float)(p.y - (double)r.yh);
-            r.il = (float)il;
+            r.il = __frcp_rn((float)__dsub_rn(1.0, n2));
             r.pad0 = r.pad1 = r.pad2 = 0.f;
             pts32[i] = r;
             const unsigned lx = __half_as_ushort(__float2half_rn(r.xl * 16777216.0f));  // lo * 2^24
             const unsigned ly = __half_as_ushort(__float2half_rn(r.yl * 16777216.0f));
             apts32[i] = PointA{r.xh, r.yh, r.il, lx | (ly << 16)};
         }
-        if (pts64) pts64[i] = PointD{p.x, p.y, il, 0.0};
+        if (pts64) pts64[i] = PointD{p.x, p.y, __ddiv_rn(1.0, __dsub_rn(1.0, n2)), 0.0};
         c = split_rule == HTS_EQUAL_AREA ? __ddiv_rn(__dadd_rn(1.0, n2), __dsub_rn(1.0, n2)) : __dsqrt_rn(n2);
         radial[i] = c;
         if (seg_of) sg = seg_of[i];

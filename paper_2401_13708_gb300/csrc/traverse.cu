@@ -107,7 +107,7 @@ __device__ __forceinline__ void record_cost(const BlockOrder &bo, int b, long lo
 // lane gets exactly the interactions of its full walk.
 constexpr int kMaxSplitDepth = 3;
 constexpr int kMaxFrontier = 64;           // 4^3
-constexpr int64_t kSplitMaxN = 262144;     // larger problems fill the GPU with chunks alone
+constexpr int64_t kSplitMaxN = 1 << 19;    // above: chunks alone fill the GPU (a cut measured slower at 1M)
 constexpr int64_t kSplitEntries = 1 << 22; // partial-sum buffer: entries x points
 
 struct Frontier {

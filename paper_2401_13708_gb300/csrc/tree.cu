@@ -457,7 +457,9 @@ __global__ void emit_kernel(EmitArgs A)
             cy = my * rd;
         }
         double beta = __dsub_rn(1.0, __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)));
-        double il = 1.0 / beta;
+        // 1 / beta: a float64 division for float64 nodes; float32 nodes store a
+        // float, taken as the float reciprocal of beta (off the float64 pipe)
+        const double il = A.nodes64 ? 1.0 / beta : 0.0;
         const uint64_t key = A.keys[lo];
         const int seg = (int)(key >> kSegShift);  // segment: its own root annulus
         double lob = __longlong_as_double((long long)A.mm[2 * seg]);
@@ -490,7 +492,7 @@ __global__ void emit_kernel(EmitArgs A)
             nd.yh = (float)cy;
             nd.xl = (float)(cx - (double)nd.xh);
             nd.yl = (float)(cy - (double)nd.yh);
-            nd.il = (float)il;
+            nd.il = __frcp_rn((float)beta);
             nd.thr = bucket ? __int_as_float(lo) : thr32;
             nd.count = bucket ? -count : count;
             nd.skip = skip;
