@@ -287,7 +287,8 @@ HTS_API int hts_set_graphs(hts_ctx *ctx, int enable);
  * stream with CUDA events, keeps the fastest and writes the choice to
  * tuning[2] = {walk threads per block, attraction lanes per row} (may be
  * NULL); for a small problem it also picks the split walk's cut depth
- * (hts_get_walk_split).  It changes no result of the walk (the work split per warp does not
+ * (hts_get_walk_split).  A smaller walk block is kept only if it is 3% faster
+ * than the larger ones.  It changes no result of the walk (the work split per warp does not
  * depend on the block size); lanes per row change only the float32 summation
  * order inside a row.  hts_set_tuning sets them directly (0 keeps a value),
  * hts_get_tuning reads them.  Defaults: {256, 8}.  Errors: HTS_ENOTSET,
