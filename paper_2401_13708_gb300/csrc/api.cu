@@ -475,6 +475,9 @@ int hts_create(hts_ctx **out, const hts_config *cfg)
     cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (cudaStreamCreateWithPriority(&c->astream, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
         cudaStreamCreateWithPriority(&c->pstream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->tstream, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->tev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->tev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->aev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->aev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->pev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -497,6 +500,7 @@ void hts_destroy(hts_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
     if (c->pstream) cudaStreamSynchronize(c->pstream);
     if (c->astream) cudaStreamSynchronize(c->astream);
+    if (c->tstream) cudaStreamSynchronize(c->tstream);
     if (c->gstream) cudaStreamSynchronize(c->gstream);
     dfree(&c->indptr); dfree(&c->indices); dfree(&c->values);
     dfree(&c->y); dfree(&c->vel); dfree(&c->gains); dfree(&c->fattr); dfree(&c->frep);
@@ -517,6 +521,9 @@ void hts_destroy(hts_ctx *c)
     if (c->gev_out) cudaEventDestroy(c->gev_out);
     if (c->astream) cudaStreamDestroy(c->astream);
     if (c->pstream) cudaStreamDestroy(c->pstream);
+    if (c->tstream) cudaStreamDestroy(c->tstream);
+    if (c->tev_fork) cudaEventDestroy(c->tev_fork);
+    if (c->tev_join) cudaEventDestroy(c->tev_join);
     if (c->aev_fork) cudaEventDestroy(c->aev_fork);
     if (c->aev_join) cudaEventDestroy(c->aev_join);
     if (c->pev_in) cudaEventDestroy(c->pev_in);

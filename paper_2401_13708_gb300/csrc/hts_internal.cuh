@@ -105,6 +105,11 @@ struct hts_ctx {
     // key / sort / tree / walk kernels leave free
     cudaStream_t pstream = nullptr;
     cudaEvent_t pev_in = nullptr, pev_out = nullptr;
+    // the tree build's two independent chains (sorted records + fixed-point
+    // sums; radix tree + layout) run side by side: tstream (highest
+    // priority) takes the first, forked and joined by events
+    cudaStream_t tstream = nullptr;
+    cudaEvent_t tev_fork = nullptr, tev_join = nullptr;
     int sm_count = 0;
     std::string err;
 

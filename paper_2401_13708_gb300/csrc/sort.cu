@@ -4,18 +4,20 @@
 // by key puts every cell's points in one contiguous run.  Eight stable
 // passes of 8 bits each (58 key bits + 6 segment bits), one kernel per pass:
 //   digit_hist  once per sort: the global histograms of all eight digits
-//               (they do not depend on the order of the keys), then an
-//               exclusive scan of each gives every digit its first slot;
+//               (they do not depend on the order of the keys; shared-memory
+//               atomics per key and digit), then an exclusive scan of each
+//               gives every digit its first slot;
 //   onesweep    per pass, one tile per block (1024, 2048 or 4096 keys by
 //               problem size, tile_keys), tiles taken in launch
-//               order from an atomic counter: warp histograms (match_any +
-//               popc), the tile's per-digit counts published to a status
-//               word, and a decoupled look-back over earlier tiles (thread d
-//               for digit d) adds up the keys of digit d before this tile;
-//               then each key is ranked among equal digits in order and
-//               written out.  Look-back spins are bounded: a timeout sets a
-//               status bit (reported as an error), and out-of-range
-//               positions are never written.
+//               order from an atomic counter: warp histograms (the lanes
+//               sharing a digit from eight ballots, one per digit bit), the
+//               tile's per-digit counts published to a status word, and a
+//               decoupled look-back over earlier tiles (thread d for digit
+//               d, kLookBack status words per round trip) adds up the keys
+//               of digit d before this tile; then each key is ranked among
+//               equal digits in order and written out.  Look-back spins are
+//               bounded: a timeout sets a status bit (reported as an
+//               error), and out-of-range positions are never written.
 // Traffic per pass: 12 B read + 12 B write per key (+ 8 B read once for the
 // histograms).
 #include <cuda/atomic>
@@ -40,6 +42,7 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;   // tile count published
 constexpr unsigned long long kFlagPre = 2ull << 62;   // inclusive prefix published
 constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookBack = 8;  // status words loaded per look-back round trip
 
 // Keys per one-sweep tile.  A pass is latency-bound: one block ranks and
 // writes its tile in kTile / 256 sequential rounds, so smaller tiles finish
@@ -60,8 +63,6 @@ __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint64_t
     __shared__ int h[kPasses][256];
     for (int k = threadIdx.x; k < kPasses * 256; k += kSortThreads) (&h[0][0])[k] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const int base = blockIdx.x * kTile;
     for (int r = 0; r < kTile / kSortThreads; ++r) {
         const int i = base + r * kSortThreads + threadIdx.x;
@@ -69,9 +70,7 @@ __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint64_t
         const uint64_t key = ok ? keys[i] : 0ull;
 #pragma unroll
         for (int p = 0; p < kPasses; ++p) {
-            const int d = ok ? (int)((key >> (8 * p)) & 0xFFu) : 256 + lane;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (ok && (peers & lt) == 0u) atomicAdd(&h[p][d], __popc(peers));
+            if (ok) atomicAdd(&h[p][(int)((key >> (8 * p)) & 0xFFu)], 1);
         }
     }
     __syncthreads();
@@ -129,16 +128,24 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
     const unsigned lt = (1u << lane) - 1u;
     uint64_t key[kRounds];
     uint32_t val[kRounds];
-    int dig[kRounds];
+    unsigned peers[kRounds];  // lanes of the round with the same digit (kept for the scatter)
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         int i = base + r * 32 + lane;
         bool ok = i < n;
         key[r] = ok ? kin[i] : 0ull;
         val[r] = ok ? vin[i] : 0u;
-        dig[r] = ok ? (int)((key[r] >> shift) & 0xFFu) : 256 + lane;  // invalid lanes match only themselves
-        unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
-        if (ok && (peers & lt) == 0u) wh[w][dig[r]] += __popc(peers);
+        const int dg = (int)((key[r] >> shift) & 0xFFu);
+        // lanes with the same digit, from eight ballots (an invalid lane matches only itself)
+        const unsigned valid = __ballot_sync(0xffffffffu, ok);  // (every lane takes part)
+        unsigned m = ok ? valid : (1u << lane);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (dg >> b) & 1);
+            m &= ((dg >> b) & 1) ? bb : ~bb;
+        }
+        peers[r] = m;
+        if (ok && (m & lt) == 0u) wh[w][dg] += __popc(m);
         __syncwarp();
     }
     __syncthreads();
@@ -159,23 +166,40 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
             if (!withhold_first) mine.store(kFlagPre | (unsigned long long)cnt, cuda::memory_order_relaxed);
         } else {
             mine.store(kFlagAgg | (unsigned long long)cnt, cuda::memory_order_relaxed);
-            // decoupled look-back: add tile counts until an inclusive prefix
-            for (int t = tile - 1; t >= 0; --t) {
-                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> other(
-                    tile_status[(size_t)t * 256 + d]);
-                unsigned long long v = other.load(cuda::memory_order_relaxed);
-                int spins = 0;
-                while ((v >> 62) == 0ull && ++spins < spin_limit) {
-                    __nanosleep(64);
-                    v = other.load(cuda::memory_order_relaxed);
+            // decoupled look-back: add tile counts until an inclusive prefix,
+            // kLookBack earlier tiles per round trip (their loads are
+            // independent; a tile whose word is not yet published is waited
+            // for in order).  Tile 0 always holds an inclusive prefix, so the
+            // walk ends there at the latest.
+            bool done = false;
+            for (int t = tile - 1; t >= 0 && !done; t -= kLookBack) {
+                unsigned long long v[kLookBack];
+#pragma unroll
+                for (int j = 0; j < kLookBack; ++j)
+                    v[j] = t - j >= 0 ? cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(
+                                            tile_status[(size_t)(t - j) * 256 + d])
+                                            .load(cuda::memory_order_relaxed)
+                                      : 0ull;
+#pragma unroll
+                for (int j = 0; j < kLookBack; ++j) {
+                    if (done || t - j < 0) break;
+                    unsigned long long vj = v[j];
+                    int spins = 0;
+                    while ((vj >> 62) == 0ull && ++spins < spin_limit) {
+                        __nanosleep(64);
+                        vj = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(
+                                 tile_status[(size_t)(t - j) * 256 + d])
+                                 .load(cuda::memory_order_relaxed);
+                    }
+                    if ((vj >> 62) == 0ull) {  // gave up: report (HTS_ETIMEOUT), positions invalid
+                        atomicOr(status, 128);
+                        excl = (long long)n;
+                        done = true;
+                        break;
+                    }
+                    excl += (long long)(vj & kValMask);
+                    done = (vj & kFlagPre) && !(vj & kFlagAgg);
                 }
-                if ((v >> 62) == 0ull) {  // gave up: report (HTS_ETIMEOUT), positions invalid
-                    atomicOr(status, 128);
-                    excl = (long long)n;
-                    break;
-                }
-                excl += (long long)(v & kValMask);
-                if ((v & kFlagPre) && !(v & kFlagAgg)) break;
             }
             mine.store(kFlagPre | (unsigned long long)(excl + cnt), cuda::memory_order_relaxed);
         }
@@ -188,11 +212,11 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
     for (int r = 0; r < kRounds; ++r) {
         int i = base + r * 32 + lane;
         bool ok = i < n;
-        unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+        const int dg = (int)((key[r] >> shift) & 0xFFu);
         int pos = 0;
-        if (ok) pos = wh[w][dig[r]] + __popc(peers & lt);
+        if (ok) pos = wh[w][dg] + __popc(peers[r] & lt);
         __syncwarp();
-        if (ok && (peers & lt) == 0u) wh[w][dig[r]] += __popc(peers);
+        if (ok && (peers[r] & lt) == 0u) wh[w][dg] += __popc(peers[r]);
         __syncwarp();
         if (ok) {
             if (pos >= 0 && pos < n) {

@@ -436,27 +436,32 @@ __global__ void emit_kernel(EmitArgs A)
         int pos = A.pre[lo] + rank;
         int skip = A.pre[hi + 1];
         const FX3 p1 = A.prefix[hi + 1], p0 = A.prefix[lo];
-        const int E = fx_exponent(*A.gmax, n);
-        const double sg = fx_to_double(p1.g - p0.g, E);
-        const double sux = fx_to_double(p1.x - p0.x, E);
-        const double suy = fx_to_double(p1.y - p0.y, E);
-        double mx, my, sq, cx, cy;
+        double mx, my, sq, cx, cy, beta;
         if (A.nodes64 || A.ex.depth) {  // float64 walk / export: the oracle's correctly rounded steps
+            const int E = fx_exponent(*A.gmax, n);
+            const double sg = fx_to_double(p1.g - p0.g, E);
+            const double sux = fx_to_double(p1.x - p0.x, E);
+            const double suy = fx_to_double(p1.y - p0.y, E);
             mx = __ddiv_rn(sux, sg);
             my = __ddiv_rn(suy, sg);
             sq = __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))));
             cx = __ddiv_rn(mx, __dadd_rn(1.0, sq));
             cy = __ddiv_rn(my, __dadd_rn(1.0, sq));
-        } else {  // float32 nodes: two reciprocals instead of four divisions
+            beta = __dsub_rn(1.0, __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)));
+        } else {
+            // float32 nodes: the sums stay scaled by 2^E (it cancels in the
+            // ratios), two reciprocals instead of four divisions, and
+            // 1 - |y_cell|^2 = 2 sq / (1 + sq)
+            const double sg = fx_to_double(p1.g - p0.g, 0);
             const double rs = 1.0 / sg;
-            mx = sux * rs;
-            my = suy * rs;
+            mx = fx_to_double(p1.x - p0.x, 0) * rs;
+            my = fx_to_double(p1.y - p0.y, 0) * rs;
             sq = sqrt(1.0 - (mx * mx + my * my));
             const double rd = 1.0 / (1.0 + sq);
             cx = mx * rd;
             cy = my * rd;
+            beta = 2.0 * sq * rd;
         }
-        double beta = __dsub_rn(1.0, __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)));
         // 1 / beta: a float64 division for float64 nodes; float32 nodes store a
         // float, taken as the float reciprocal of beta (off the float64 pipe)
         const double il = A.nodes64 ? 1.0 / beta : 0.0;
@@ -583,25 +588,35 @@ void launch_build_tree(hts_ctx *c, double theta, const TreeExport *ex)
     const bool f32 = c->cfg.precision == HTS_FP32_MIXED;
     const int gp = (n + kBlock - 1) / kBlock;
     unsigned long long *gmax = c->minmax + 2 * kMaxSegments;
-    cudaMemsetAsync(gmax, 0, sizeof(unsigned long long), s);
-    gather_kernel<<<gp, kBlock, 0, s>>>(n, c->idx, c->y, c->pts32, c->pts64, f32 ? c->spts32 : nullptr,
-                                        f32 ? nullptr : c->spts64, c->terms, gmax, (!f32 || ex) ? 1 : 0);
-    c->launches += 4;  // gather, quad_mark, count, emit
     FX3 *prefix = reinterpret_cast<FX3 *>(c->bn_sum);  // n + 1 entries
     unsigned *mask = reinterpret_cast<unsigned *>(c->bn_flag);
+    cudaMemsetAsync(gmax, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(mask, 0, sizeof(unsigned) * (size_t)n, s);
+    // two independent chains, joined before emit: on the side stream the
+    // sorted point records and the fixed-point prefix sums of the Einstein
+    // terms; here the radix tree, the quad-level marks and the node layout
+    // (they need only the sorted keys)
+    cudaStream_t ts = c->tstream;
+    cudaEventRecord(c->tev_fork, s);
+    cudaStreamWaitEvent(ts, c->tev_fork, 0);
+    gather_kernel<<<gp, kBlock, 0, ts>>>(n, c->idx, c->y, c->pts32, c->pts64, f32 ? c->spts32 : nullptr,
+                                         f32 ? nullptr : c->spts64, c->terms, gmax, (!f32 || ex) ? 1 : 0);
+    c->launches += 4;  // gather, quad_mark, count, emit
+    if (n > 1)
+        fx_scan(n, c->terms, gmax, n, nullptr, prefix, prefix + n, reinterpret_cast<FX3 *>(c->red_tmp), ts,
+                &c->launches);
+    cudaEventRecord(c->tev_join, ts);
     if (n > 1) {
         const int gi = (n - 1 + kBlock - 1) / kBlock;
         radix_tree_kernel<<<gi, kBlock, 0, s>>>(n, c->keys, c->bn_left, c->bn_right, c->bn_parent, c->leaf_parent,
                                                 c->bn_lo, c->bn_hi, c->bn_pref);
         c->launches += 1;
-        fx_scan(n, c->terms, gmax, n, nullptr, prefix, prefix + n, reinterpret_cast<FX3 *>(c->red_tmp), s,
-                &c->launches);
         quad_mark_kernel<<<gp, kBlock, 0, s>>>(n, c->bn_parent, c->leaf_parent, c->bn_lo, c->bn_pref, c->bn_quad,
                                                mask);
     }
     count_kernel<<<(n + 1 + kBlock - 1) / kBlock, kBlock, 0, s>>>(n, c->leaf_parent, c->bn_pref, mask, c->cnt);
     c->launches += scan_exclusive(c->cnt, c->pre, (int64_t)n + 1, c->scan_tmp, s);
+    cudaStreamWaitEvent(s, c->tev_join, 0);
     EmitArgs A;
     A.n = n;
     A.theta = theta;
