@@ -46,11 +46,11 @@ __global__ void prep_points_kernel(int n, const double2 *__restrict__ y, int spl
         double n2 = __dadd_rn(__dmul_rn(p.x, p.x), __dmul_rn(p.y, p.y));
         if (pts32) {  // il as the float reciprocal of 1 - |y|^2 (off the float64 pipe)
             PointF r;
-            r.xh = (float)p.x;
-            r.yh = (float)p.y;
-            r.xl = (float)(p.x - (double)r.xh);
-            r.yl = (float)(p.y - (double)r.yh);
-            r.il = __frcp_rn((float)__dsub_rn(1.0, n2));
+            float a32, unused;
+            split_f32(p.x, r.xh, r.xl);
+            split_f32(p.y, r.yh, r.yl);
+            split_f32(__dsub_rn(1.0, n2), a32, unused);  // (float)(1 - |y|^2)
+            r.il = __frcp_rn(a32);
             r.pad0 = r.pad1 = r.pad2 = 0.f;
             pts32[i] = r;
             const unsigned lx = __half_as_ushort(__float2half_rn(r.xl * 16777216.0f));  // lo * 2^24
@@ -95,12 +95,21 @@ __device__ __forceinline__ uint64_t spread_bits(uint64_t v)
     return v;
 }
 
+// floor(u 2^kLevels) clamped to [0, 2^kLevels - 1] (negative and NaN -> 0,
+// +inf -> the top), from the bit pattern of u with integer operations: the
+// float64 route (multiply, floor, convert) runs on the narrow float64 pipe.
 __device__ __forceinline__ uint64_t quantise(double u)
 {
-    double s = floor(__dmul_rn(u, (double)(1u << kLevels)));
-    uint64_t q = (uint64_t)s;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
     const uint64_t top = (1ull << kLevels) - 1;
-    return q > top ? top : q;
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const unsigned long long mant = b & ((1ull << 52) - 1ull);
+    if (ex == 0x7ff) return (mant || (b >> 63)) ? 0ull : top;  // NaN, -inf; +inf
+    if (b >> 63) return 0ull;                                   // negative, -0
+    if (ex >= 1023) return top;                                 // u >= 1
+    const unsigned long long S = ex ? mant | (1ull << 52) : mant;
+    const int shift = 1075 - kLevels - (ex ? ex : 1);           // u 2^kLevels = S 2^-shift, shift > 23
+    return shift >= 64 ? 0ull : S >> shift;
 }
 
 __global__ void make_keys_kernel(int n, const double2 *__restrict__ y, const double *__restrict__ radial,

@@ -523,11 +523,11 @@ __global__ void emit_kernel(EmitArgs A)
         }
         if (A.nodes32) {
             NodeF nd;
-            nd.xh = (float)cx;
-            nd.yh = (float)cy;
-            nd.xl = (float)(cx - (double)nd.xh);
-            nd.yl = (float)(cy - (double)nd.yh);
-            nd.il = __frcp_rn((float)beta);
+            float b32, unused;
+            split_f32(cx, nd.xh, nd.xl);
+            split_f32(cy, nd.yh, nd.yl);
+            split_f32(beta, b32, unused);  // (float)beta
+            nd.il = __frcp_rn(b32);
             nd.thr = bucket ? __int_as_float(lo) : thr32;
             nd.count = bucket ? -count : count;
             nd.skip = skip;
