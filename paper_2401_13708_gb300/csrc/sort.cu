@@ -7,8 +7,9 @@
 //               (they do not depend on the order of the keys; shared-memory
 //               atomics per key and digit), then an exclusive scan of each
 //               gives every digit its first slot;
-//   onesweep    per pass, one tile per block (1024, 2048 or 4096 keys by
-//               problem size, tile_keys), tiles taken in launch
+//   onesweep    per pass, one tile per block (1024, 2048 or 4096 keys of
+//               256 threads, or 8192 keys of 512 threads, by problem size:
+//               tile_keys), tiles taken in launch
 //               order from an atomic counter: warp histograms (the lanes
 //               sharing a digit from eight ballots, one per digit bit), the
 //               tile's per-digit counts published to a status word, and a
@@ -43,16 +44,21 @@ constexpr unsigned long long kFlagPre = 2ull << 62;   // inclusive prefix publis
 constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookBack = 8;  // status words loaded per look-back round trip
+constexpr int64_t kBigTileFrom = 524288;  // above this, 8192-key tiles of 512 threads
 
 // Keys per one-sweep tile.  A pass is latency-bound: one block ranks and
 // writes its tile in kTile / 256 sequential rounds, so smaller tiles finish
-// sooner while there are SMs to spare; large problems keep 4096-key tiles
-// (fewer look-back steps and status words).  Measured sort times per
-// iteration: 20,000 keys 156 / 110 / 87 us with 4096 / 2048 / 1024-key tiles,
-// 262,145 keys 174 / 143 / 152 us, 1,000,000 keys 283 / 295 / 301 us.
+// sooner while there are SMs to spare; large problems take larger tiles
+// (fewer look-back steps and status words: every tile of a pass is resident
+// at once, so the last tile looks back over nearly all of them).  Measured
+// sort times per iteration: 20,000 keys 156 / 110 / 87 us with 4096 / 2048 /
+// 1024-key tiles, 262,145 keys 174 / 143 / 152 us, 1,000,000 keys 283 / 295 /
+// 301 us (before the ballot ranking and the batched look-back); with them,
+// 1,000,000 keys 198 us with 4096-key tiles and 185 us with 8192 keys of 512
+// threads (700,000 keys: 181 / 180 us).
 int tile_keys(int64_t n)
 {
-    return n <= 196608 ? 1024 : n <= 524288 ? 2048 : 4096;
+    return n <= 196608 ? 1024 : n <= 524288 ? 2048 : n <= kBigTileFrom ? 4096 : 8192;
 }
 
 // Global histograms of all eight digits; hist[pass][digit] (2048 ints).
@@ -105,8 +111,8 @@ __global__ void digit_offsets_kernel(int *hist)
     }
 }
 
-template <int kTile>
-__global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *__restrict__ kin,
+template <int kTile, int kThreads = kSortThreads>
+__global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t *__restrict__ kin,
                                                                 const uint32_t *__restrict__ vin,
                                                                 uint64_t *__restrict__ kout,
                                                                 uint32_t *__restrict__ vout, int n, int shift,
@@ -114,12 +120,13 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
                                                                 unsigned long long *tile_status, int *tile_ctr,
                                                                 int *status, int spin_limit, int withhold_first)
 {
-    constexpr int kPerWarp = kTile / kWarps;
+    constexpr int kW = kThreads / 32;  // warps per tile
+    constexpr int kPerWarp = kTile / kW;
     constexpr int kRounds = kPerWarp / 32;
-    __shared__ int wh[kWarps][256];
+    __shared__ int wh[kW][256];
     __shared__ int s_tile;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
+    for (int k = threadIdx.x; k < kW * 256; k += kThreads) (&wh[0][0])[k] = 0;
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1);  // tiles in launch order
     __syncthreads();
     const int tile = s_tile;
@@ -149,11 +156,11 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
         __syncwarp();
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;  // 256 threads = 256 digits
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;  // the first 256 threads: one digit each
         int cnt = 0;
 #pragma unroll
-        for (int k = 0; k < kWarps; ++k) {
+        for (int k = 0; k < kW; ++k) {
             const int t = wh[k][d];
             wh[k][d] = cnt;  // exclusive prefix over the warps of this tile
             cnt += t;
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(const uint64_t *
         }
         const int off = digit_off[d] + (int)min(excl, (long long)n);
 #pragma unroll
-        for (int k = 0; k < kWarps; ++k) wh[k][d] += off;
+        for (int k = 0; k < kW; ++k) wh[k][d] += off;
     }
     __syncthreads();
 #pragma unroll
@@ -426,8 +433,10 @@ void launch_sort_pairs(hts_ctx *c)
         digit_hist_kernel<1024><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
     else if (tile == 2048)
         digit_hist_kernel<2048><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
-    else
+    else if (tile == 4096)
         digit_hist_kernel<4096><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
+    else
+        digit_hist_kernel<8192><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
     digit_offsets_kernel<<<1, 32 * kPasses, 0, c->stream>>>(hist);
     c->launches += 2 + kPasses;
     uint64_t *ka = c->keys, *kb = c->keys_alt;
@@ -442,9 +451,12 @@ void launch_sort_pairs(hts_ctx *c)
         else if (tile == 2048)
             onesweep_kernel<2048><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
                                                                          sp, ctr + p, c->status, spin, hold);
-        else
+        else if (tile == 4096)
             onesweep_kernel<4096><<<tiles, kSortThreads, 0, c->stream>>>(ka, va, kb, vb, n, 8 * p, hist + p * 256,
                                                                          sp, ctr + p, c->status, spin, hold);
+        else
+            onesweep_kernel<8192, 2 * kSortThreads><<<tiles, 2 * kSortThreads, 0, c->stream>>>(
+                ka, va, kb, vb, n, 8 * p, hist + p * 256, sp, ctr + p, c->status, spin, hold);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }

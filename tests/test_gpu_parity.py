@@ -88,8 +88,9 @@ def test_tree_matches_oracle(name, rule):
 def test_tree_across_sort_paths(n):
     """The key sort runs in one block up to 4096 keys and as one-sweep passes
     with decoupled look-back above, in tiles of 1024 keys up to 196,608 keys,
-    2048 up to 524,288 and 4096 beyond; both sides of every boundary build the
-    oracle's tree.  (P plays no part in the tree: it is empty here.)"""
+    2048 up to 524,288 and 8192 (512 threads) beyond; both sides of every
+    boundary build the oracle's tree.  (P plays no part in the tree: it is
+    empty here.)"""
     labels = (np.arange(n) * 7919) % 37
     y = inputs.spread_embedding(labels, n % 5, rho_hi=10.0)
     with HyperbolicTSNE(precision="fp32") as t:
