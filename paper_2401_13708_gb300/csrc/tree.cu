@@ -466,31 +466,31 @@ __global__ void emit_kernel(EmitArgs A)
         int pos = A.pre[lo] + rank;
         int skip = A.pre[hi + 1];
         const FX3 p1 = A.prefix[hi + 1], p0 = A.prefix[lo];
-        double mx, my, sq, cx, cy, beta;
+        double cx, cy, beta;
         if (A.nodes64 || A.ex.depth) {  // float64 walk / export: the oracle's correctly rounded steps
             const int E = fx_exponent(*A.gmax, n);
             const double sg = fx_to_double(p1.g - p0.g, E);
             const double sux = fx_to_double(p1.x - p0.x, E);
             const double suy = fx_to_double(p1.y - p0.y, E);
-            mx = __ddiv_rn(sux, sg);
-            my = __ddiv_rn(suy, sg);
-            sq = __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))));
+            const double mx = __ddiv_rn(sux, sg);
+            const double my = __ddiv_rn(suy, sg);
+            const double sq = __dsqrt_rn(__dsub_rn(1.0, __dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my))));
             cx = __ddiv_rn(mx, __dadd_rn(1.0, sq));
             cy = __ddiv_rn(my, __dadd_rn(1.0, sq));
             beta = __dsub_rn(1.0, __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)));
         } else {
-            // float32 nodes: the sums stay scaled by 2^E (it cancels in the
-            // ratios), two reciprocals instead of four divisions, and
-            // 1 - |y_cell|^2 = 2 sq / (1 + sq)
+            // float32 nodes: the sums stay scaled by 2^E (it cancels), and
+            // with m = S_u / S_g and R = sqrt(S_g^2 - |S_u|^2) = S_g sq,
+            //   y_cell = m / (1 + sq) = S_u / (S_g + R),
+            //   1 - |y_cell|^2 = 2 sq / (1 + sq) = 2 R / (S_g + R):
+            // one reciprocal instead of two
             const double sg = fx_to_double_unscaled(p1.g - p0.g);
-            const double rs = 1.0 / sg;
-            mx = fx_to_double_unscaled(p1.x - p0.x) * rs;
-            my = fx_to_double_unscaled(p1.y - p0.y) * rs;
-            sq = sqrt(1.0 - (mx * mx + my * my));
-            const double rd = 1.0 / (1.0 + sq);
-            cx = mx * rd;
-            cy = my * rd;
-            beta = 2.0 * sq * rd;
+            const double sux = fx_to_double_unscaled(p1.x - p0.x), suy = fx_to_double_unscaled(p1.y - p0.y);
+            const double R = sqrt(fmax(sg * sg - (sux * sux + suy * suy), 0.0));
+            const double rd = 1.0 / (sg + R);
+            cx = sux * rd;
+            cy = suy * rd;
+            beta = 2.0 * R * rd;
         }
         // 1 / beta: a float64 division for float64 nodes; float32 nodes store a
         // float, taken as the float reciprocal of beta (off the float64 pipe)

@@ -89,6 +89,23 @@ struct UpdateArgs {
     const int64_t *seg_off;       // batched: segment offsets (CO-SNE uses the segment's n)
 };
 
+// tanh for the exp map's argument lambda |v| / 2 >= 0, which is small for the
+// steps of the optimiser: below 2^-5 the Taylor series
+//   tanh x = x - x^3/3 + 2 x^5/15 - 17 x^7/315 + 62 x^9/2835 - ...
+// to the x^9 term (truncation below 1e-17 relative there), else tanh.
+__device__ __forceinline__ double tanh_step(double x)
+{
+    if (x < 0.03125) {
+        const double t = x * x;
+        double p = 62.0 / 2835.0;
+        p = fma(p, t, -17.0 / 315.0);
+        p = fma(p, t, 2.0 / 15.0);
+        p = fma(p, t, -1.0 / 3.0);
+        return fma(x * t, p, x);
+    }
+    return tanh(x);
+}
+
 __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
 {
     __shared__ double s_invz;
@@ -150,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) update_kernel(UpdateArgs A)
         // exp map: p (+) tanh(lambda |v| / 2) v / |v|, lambda |v| / 2 = |v| / a;
         // 1 / |v| from one reciprocal square root (no square root and division)
         const double rn = rsqrt(vv), nv = vv * rn;
-        const double f = tanh(nv / a) * rn;
+        const double f = tanh_step(nv / a) * rn;
         const double ux = f * v.x, uy = f * v.y;
         const double pu = p.x * ux + p.y * uy;
         const double nu = ux * ux + uy * uy;
