@@ -61,6 +61,21 @@ int tile_keys(int64_t n)
     return n <= 196608 ? 1024 : n <= 524288 ? 2048 : n <= kBigTileFrom ? 4096 : 8192;
 }
 
+// The lanes of the warp whose 8-bit digit equals this lane's, from eight
+// ballots (one per digit bit); a lane that is not `ok` matches only itself.
+// Every lane of the warp makes the call.
+__device__ __forceinline__ unsigned digit_peers(int dg, bool ok, int lane)
+{
+    const unsigned valid = __ballot_sync(0xffffffffu, ok);
+    unsigned m = ok ? valid : (1u << lane);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (dg >> b) & 1);
+        m &= ((dg >> b) & 1) ? bb : ~bb;
+    }
+    return m;
+}
+
 // Global histograms of all eight digits; hist[pass][digit] (2048 ints).
 template <int kTile>
 __global__ void __launch_bounds__(kSortThreads) digit_hist_kernel(const uint64_t *__restrict__ keys, int n,
@@ -143,14 +158,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const uint64_t *__re
         key[r] = ok ? kin[i] : 0ull;
         val[r] = ok ? vin[i] : 0u;
         const int dg = (int)((key[r] >> shift) & 0xFFu);
-        // lanes with the same digit, from eight ballots (an invalid lane matches only itself)
-        const unsigned valid = __ballot_sync(0xffffffffu, ok);  // (every lane takes part)
-        unsigned m = ok ? valid : (1u << lane);
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const unsigned bb = __ballot_sync(0xffffffffu, (dg >> b) & 1);
-            m &= ((dg >> b) & 1) ? bb : ~bb;
-        }
+        const unsigned m = digit_peers(dg, ok, lane);
         peers[r] = m;
         if (ok && (m & lt) == 0u) wh[w][dg] += __popc(m);
         __syncwarp();
@@ -340,16 +348,16 @@ __global__ void __launch_bounds__(kSortThreads) small_sort_kernel(uint64_t *ka, 
         __syncthreads();
         uint64_t key[kRounds];
         uint32_t val[kRounds];
-        int dig[kRounds];
+        unsigned peers[kRounds];
 #pragma unroll
         for (int r = 0; r < kRounds; ++r) {
             const int i = base + r * 32 + lane;
             const bool ok = i < n;
             key[r] = ok ? kin[i] : 0ull;
             val[r] = ok ? vin[i] : 0u;
-            dig[r] = ok ? (int)((key[r] >> shift) & 0xFFu) : 256 + lane;
-            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
-            if (ok && (peers & lt) == 0u) wh[w][dig[r]] += __popc(peers);
+            const int dg = (int)((key[r] >> shift) & 0xFFu);
+            peers[r] = digit_peers(dg, ok, lane);
+            if (ok && (peers[r] & lt) == 0u) wh[w][dg] += __popc(peers[r]);
             __syncwarp();
         }
         __syncthreads();
@@ -384,11 +392,11 @@ __global__ void __launch_bounds__(kSortThreads) small_sort_kernel(uint64_t *ka, 
         for (int r = 0; r < kRounds; ++r) {
             const int i = base + r * 32 + lane;
             const bool ok = i < n;
-            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+            const int dg = (int)((key[r] >> shift) & 0xFFu);
             int pos = 0;
-            if (ok) pos = wh[w][dig[r]] + __popc(peers & lt);
+            if (ok) pos = wh[w][dg] + __popc(peers[r] & lt);
             __syncwarp();
-            if (ok && (peers & lt) == 0u) wh[w][dig[r]] += __popc(peers);
+            if (ok && (peers[r] & lt) == 0u) wh[w][dg] += __popc(peers[r]);
             __syncwarp();
             if (ok && pos >= 0 && pos < n) {
                 kout[pos] = key[r];
