@@ -437,14 +437,15 @@ void launch_sort_pairs(hts_ctx *c)
     unsigned long long *stat = reinterpret_cast<unsigned long long *>(c->sort_scratch + (kPasses * 256 + 64) / 2);
     cudaMemsetAsync(c->sort_scratch, 0, sizeof(unsigned long long) * ((kPasses * 256 + 64) / 2 +
                                                                       (size_t)kPasses * 256 * tiles), c->stream);
+    // (the histograms do not depend on the pass tiles: at most 4096 keys per
+    // block keeps enough blocks in flight)
+    const int hblocks = (n + 4095) / 4096;
     if (tile == 1024)
         digit_hist_kernel<1024><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
     else if (tile == 2048)
         digit_hist_kernel<2048><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
-    else if (tile == 4096)
-        digit_hist_kernel<4096><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
     else
-        digit_hist_kernel<8192><<<tiles, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
+        digit_hist_kernel<4096><<<hblocks, kSortThreads, 0, c->stream>>>(c->keys, n, hist);
     digit_offsets_kernel<<<1, 32 * kPasses, 0, c->stream>>>(hist);
     c->launches += 2 + kPasses;
     uint64_t *ka = c->keys, *kb = c->keys_alt;
