@@ -24,6 +24,7 @@
 #include <string>
 
 #include "../../include/hts.h"
+#include "bits.cuh"
 
 namespace hts {
 
@@ -39,37 +40,6 @@ struct __align__(16) PointF {
     float xh, yh, xl, yl;
     float il, pad0, pad1, pad2;
 };
-
-// hi = c rounded to float32 (to nearest, ties to even) and lo = c - hi rounded
-// to float32: the same values as the two conversions, taken from the bit
-// pattern of c with integer operations (float64 conversions run on the
-// narrow float64 pipe of this GPU).  |c| in [2^-60, 2^100): lo is then a
-// normal float and exact up to its rounding; other values (zero included)
-// take the conversions.
-__device__ __forceinline__ void split_f32(double c, float &hi, float &lo)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(c);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex < 1023 - 60 || ex >= 1023 + 100) {
-        hi = (float)c;
-        lo = (float)(c - (double)hi);
-        return;
-    }
-    const unsigned long long S = (b & ((1ull << 52) - 1ull)) | (1ull << 52);  // 53-bit significand
-    unsigned long long h = S >> 29;                                            // top 24 bits
-    const unsigned long long r = S & ((1ull << 29) - 1ull);
-    if (r > (1ull << 28) || (r == (1ull << 28) && (h & 1ull))) ++h;           // to nearest, ties to even
-    const int rem = (int)((long long)S - (long long)(h << 29));                // c - hi in units of 2^(ex - 1075)
-    int e = ex;
-    if (h == (1ull << 24)) {  // rounded up into the next binade
-        h >>= 1;
-        ++e;
-    }
-    const unsigned sgn = (unsigned)(b >> 63) << 31;
-    hi = __uint_as_float(sgn | ((unsigned)(e - 1023 + 127) << 23) | ((unsigned)h & 0x7fffffu));
-    const float unit = __uint_as_float((unsigned)(ex - 1075 + 127) << 23);   // 2^(ex - 1075), normal
-    lo = __int2float_rn(sgn ? -rem : rem) * unit;  // |rem| <= 2^28; the scaling is exact (+0 when c = hi)
-}
 
 // Point record of the float32 attractive sum (16 bytes: the neighbour
 // gather moves half the bytes of a PointF): hi floats and il as in PointF,

@@ -95,22 +95,10 @@ __device__ __forceinline__ uint64_t spread_bits(uint64_t v)
     return v;
 }
 
-// floor(u 2^kLevels) clamped to [0, 2^kLevels - 1] (negative and NaN -> 0,
-// +inf -> the top), from the bit pattern of u with integer operations: the
-// float64 route (multiply, floor, convert) runs on the narrow float64 pipe.
-__device__ __forceinline__ uint64_t quantise(double u)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
-    const uint64_t top = (1ull << kLevels) - 1;
-    const int ex = (int)((b >> 52) & 0x7ff);
-    const unsigned long long mant = b & ((1ull << 52) - 1ull);
-    if (ex == 0x7ff) return (mant || (b >> 63)) ? 0ull : top;  // NaN, -inf; +inf
-    if (b >> 63) return 0ull;                                   // negative, -0
-    if (ex >= 1023) return top;                                 // u >= 1
-    const unsigned long long S = ex ? mant | (1ull << 52) : mant;
-    const int shift = 1075 - kLevels - (ex ? ex : 1);           // u 2^kLevels = S 2^-shift, shift > 23
-    return shift >= 64 ? 0ull : S >> shift;
-}
+// floor(u 2^kLevels) clamped to [0, 2^kLevels - 1], from the bit pattern of u
+// (bits.cuh): the float64 route (multiply, floor, convert) runs on the narrow
+// float64 pipe.
+__device__ __forceinline__ uint64_t quantise(double u) { return quantise_unit(u, kLevels); }
 
 __global__ void make_keys_kernel(int n, const double2 *__restrict__ y, const double *__restrict__ radial,
                                  const unsigned char *__restrict__ seg_of, const unsigned long long *__restrict__ mm,

@@ -165,47 +165,11 @@ __device__ __forceinline__ int fx_exponent(unsigned long long gmax_bits, int n)
 // 2^k for -1022 <= k <= 1023 (a normal float64 built from its exponent bits).
 __device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
-// floor(x * 2^E) as a 128-bit integer (exact; x finite, |x| 2^E < 2^125):
-// the significand shifted into place with integer operations only, so the
-// conversion stays off the float64 pipe (conversions run there).
-__device__ __forceinline__ fx_t fx_from_double(double x, int E)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    unsigned long long m = b & ((1ull << 52) - 1ull);
-    if (ex) m |= 1ull << 52;
-    if (m == 0ull) return 0;
-    const int sh = (ex ? ex : 1) - 1075 + E;  // |x| 2^E = m 2^sh
-    unsigned __int128 mag;
-    bool frac = false;                        // bits below 2^0 dropped
-    if (sh >= 0) {
-        mag = (unsigned __int128)m << sh;
-    } else if (sh > -64) {
-        mag = m >> (-sh);
-        frac = (m & ((1ull << (-sh)) - 1ull)) != 0ull;
-    } else {
-        mag = 0;
-        frac = true;
-    }
-    if (!(b >> 63)) return (fx_t)mag;
-    return -(fx_t)(mag + (frac ? 1u : 0u));  // floor of a negative value
-}
-
-// |v| truncated to 53 significant bits, as a float64 with the sign of v and
-// without the 2^-E scale (float32 nodes: the scale cancels in the ratios),
-// built from its bit pattern with integer operations only.
-__device__ __forceinline__ double fx_to_double_unscaled(fx_t v)
-{
-    const bool neg = v < 0;
-    const unsigned __int128 m = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
-    const unsigned long long hi = (unsigned long long)(m >> 64), lo = (unsigned long long)m;
-    if ((hi | lo) == 0ull) return 0.0;
-    const int top = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
-    const unsigned long long mant =
-        (top >= 52 ? (unsigned long long)(m >> (top - 52)) : lo << (52 - top)) & ((1ull << 52) - 1ull);
-    const unsigned long long bits = ((unsigned long long)(top + 1023) << 52) | mant | (neg ? 1ull << 63 : 0ull);
-    return __longlong_as_double((long long)bits);
-}
+// floor(x * 2^E) and a cell sum as a float64 without the 2^-E scale (float32
+// nodes: the scale cancels in the ratios), both from bit patterns with integer
+// operations (bits.cuh), off the float64 pipe that runs the conversions.
+__device__ __forceinline__ fx_t fx_from_double(double x, int E) { return fixed_from_double(x, E); }
+__device__ __forceinline__ double fx_to_double_unscaled(fx_t v) { return fixed_to_double_trunc(v); }
 
 // v * 2^-E correctly rounded to float64: the top 64 significant bits, with a
 // sticky bit for the rest, go through one round-to-nearest conversion.
