@@ -31,7 +31,7 @@ namespace hts {
 namespace {
 
 constexpr int kSmallMax = 4096;    // up to this many keys, one block sorts (small_sort_kernel)
-constexpr int kMinTile = 1024;     // one-sweep tiles hold 1024, 2048 or 4096 keys (tile_keys)
+constexpr int kMinTile = 1024;     // one-sweep tiles hold 1024, 2048, 4096 or 8192 keys (tile_keys)
 constexpr int kSortThreads = 256;
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kScanThreads = 1024;
@@ -44,7 +44,9 @@ constexpr unsigned long long kFlagPre = 2ull << 62;   // inclusive prefix publis
 constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookBack = 8;  // status words loaded per look-back round trip
-constexpr int64_t kBigTileFrom = 524288;  // above this, 8192-key tiles of 512 threads
+// above this, 8192-key tiles of 512 threads (4096-key tiles of 256 threads
+// serve sizes between 524,288 and this bound when it is raised)
+constexpr int64_t kBigTileFrom = 524288;
 
 // Keys per one-sweep tile.  A pass is latency-bound: one block ranks and
 // writes its tile in kTile / 256 sequential rounds, so smaller tiles finish
